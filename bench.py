@@ -1,0 +1,384 @@
+"""Benchmark: F3R time-to-solution at 1e-9 on one GB300, with the fp16 SpMV /
+Richardson roofline and the fp64-FGMRES(64) / fp32-F3R comparators.
+
+One step = one full F3R solve (x0 = 0 to ||b - Ax||/||b|| < 1e-9) of the
+128^3 7-point variable-coefficient diffusion system (n = 2,097,152,
+nnz = 14,581,760), inputs resident in HBM.  L2 is flushed (a 256 MiB write)
+before every timed solve; each solve is timed with CUDA events on the calling
+stream.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (the reference arm of this build) on a
+bounded sample of the same workload.  With N > 1 (torchrun) every rank solves
+its own replica of the workload (no collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "F3R time-to-solution at 1e-9 rel. residual vs fp64 FGMRES; fp16 SpMV % of HBM BW"
+WORKLOADS = {
+    "diffusion7_128": "3-D 7-point variable-coefficient diffusion 128^3, log-normal face coefficients (sigma 1.5), "
+                      "symmetric diagonal scaling, fp16 inner storage, Jacobi M, F3R (100,8,4,2), c=64, tol 1e-9",
+    "convdiff27_160": "nonsymmetric 3-D 27-point convection-diffusion 160^3, cell Peclet in [0.1,10]",
+    "poisson2d_64": "2-D 5-point Poisson 64x64, Jacobi M unscaled",
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2505_20719_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+        e = t.get(kernel)
+        if e and e.get("src_sha") == _src_hash():
+            return e.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(prob, kind, outer_iters, max_seconds=25.0):
+    """The oracle as it stands, timed on this host's cores on a bounded sample:
+    whole outer iterations of the same solve (x0 = 0), scaled to the number of
+    outer iterations the full solve takes."""
+    import oracle as O
+    P = O.Problem(prob, diag_scale=1)
+    prm = O.preset(kind)
+    k = 1
+    t0 = time.perf_counter()
+    res = P.solve(O.preset(kind, max_outer=k), prob.b)
+    dt = time.perf_counter() - t0
+    per_iter = dt / max(1, res.outer_iters)
+    if per_iter * 2 < max_seconds and outer_iters > 1:
+        k = max(1, min(outer_iters, int(max_seconds / per_iter)))
+        t0 = time.perf_counter()
+        res = P.solve(O.preset(kind, max_outer=k), prob.b)
+        dt = time.perf_counter() - t0
+        per_iter = dt / max(1, res.outer_iters)
+    del prm
+    return {"value": per_iter * outer_iters * 1e3, "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{res.outer_iters} of {outer_iters} outer iterations of the same solve "
+                      f"({dt:.1f} s), scaled linearly to the full solve"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle as O
+    from problems import generators as G
+    prob = G.by_name(args.workload)
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_solves.json")))
+    outer = golden[args.workload][args.kind]["outer_iters"]
+    P = O.Problem(prob, diag_scale=0 if args.workload == "poisson2d_64" else 1)
+    steps = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = P.solve(O.preset(args.kind, max_outer=1,
+                               diag_scale=0 if args.workload == "poisson2d_64" else 1), prob.b)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            steps.append(dt / max(1, res.outer_iters))
+    per_iter = statistics.median(steps)
+    value = per_iter * outer * 1e3
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64 (emulated on the CPU)",
+        "data": "synthetic", "config": {"workload": args.workload, "solver": args.kind, "n": prob.n,
+                                        "nnz": prob.nnz, "tol": 1e-9, "parallelism": "replicas"},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"each step = 1 outer iteration of the solve (median of {args.steps}); "
+                                   f"scaled by the oracle's {outer} outer iterations to convergence"},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="diffusion7_128", choices=sorted(WORKLOADS))
+    ap.add_argument("--kind", default="fp16-F3R")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2505_20719_gb300 import f3r
+    from problems import generators as G
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    prob = G.by_name(args.workload)
+    ds = 0 if args.workload == "poisson2d_64" else 1
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rp, ci, va, b = T(prob.rowptr), T(prob.colidx), T(prob.val), T(prob.b)
+    prm = f3r.preset(args.kind, diag_scale=ds)
+    s = f3r.Solver(rp, ci, va, prm, stream=stream)
+    x = torch.zeros(prob.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_solve():
+        x.zero_()
+        flush.fill_(1.0)  # evict L2 (256 MiB > 129 MB) before the timed region of each solve
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = s.solve(b, x, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    for _ in range(args.warmup):
+        one_solve()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, launches, results = [], 0, []
+    for _ in range(args.steps):
+        ms, r = one_solve()
+        times.append(ms)
+        launches += r.kernel_launches
+        results.append(r)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(times)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+    last = results[-1]
+    A = prob.to_scipy()
+    xh = x.cpu().numpy()
+    true_rel = float(np.linalg.norm(prob.b - A @ xh) / np.linalg.norm(prob.b))
+    ms_per_solve = total_ms / args.steps
+    value = ms_per_solve / ws
+
+    # ---- per-kernel device time inside one solve (events on the launching stream)
+    f3r.lib().f3r_profile_enable(s.h, 1)
+    x.zero_()
+    s.solve(b, x, stream=stream)
+    torch.cuda.synchronize()
+    prof = {}
+    for slot in range(f3r.lib().f3r_profile_slots()):
+        cnt = f3r.C.c_int64()
+        tms = f3r.C.c_double()
+        f3r.lib().f3r_profile_get(s.h, slot, f3r.C.byref(cnt), f3r.C.byref(tms))
+        if cnt.value:
+            name = f3r.lib().f3r_profile_slot_name(slot).decode() + f"_L{slot % 4}"
+            prof[name] = {"launches": cnt.value, "ms": tms.value}
+    f3r.lib().f3r_profile_enable(s.h, 0)
+    tot = sum(v["ms"] for v in prof.values())
+    for v in prof.values():
+        v["share"] = v["ms"] / tot if tot else 0.0
+        v["avg_us"] = 1e3 * v["ms"] / v["launches"]
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    n, nnz = prob.n, prob.nnz
+    hbm, peak_src = _peaks()
+    # algorithmic bytes per launch of the candidate dominant kernels
+    algo = {
+        "rich_fused2_L0": 6 * nnz + 2 * n + 2 * n + 4 * n,   # A16 (val + int32 col), v16, m16, z fp32 out
+        "spmv_dots_L2": 6 * nnz + 4 * n + 4 * n + 4 * n * 2.5,  # A16, z fp32, w fp32 out, V[0..j] (avg 2.5)
+        "spmv_dots_L1": 8 * nnz + 4 * n + 4 * n + 4 * n * 4.5,  # A32, z, w, V[0..j] (avg 4.5)
+    }
+    dk = dom if dom in algo else "rich_fused2_L0"
+    avg_s = prof[dk]["avg_us"] * 1e-6
+    achieved = algo[dk] / avg_s / 1e9
+    roofline = {"bound": "hbm", "kernel": dk, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": f"{peak_src} (copy bandwidth, burst)",
+                "algorithmic_bytes_per_launch": algo[dk], "avg_launch_us": prof[dk]["avg_us"],
+                "traffic": _ncu_traffic(dk)}
+
+    # ---- stand-alone fp16 SpMV (f3r_spmv), the metric's second half
+    xs = torch.randn(n, device=dev, dtype=torch.float32)
+    ys = torch.empty(n, device=dev, dtype=torch.float32)
+    for _ in range(5):
+        s.spmv(f3r.F16, f3r.F32, xs, ys, stream=stream)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(2.0)
+    e0.record(stream)
+    for _ in range(reps):
+        s.spmv(f3r.F16, f3r.F32, xs, ys, stream=stream)
+    e1.record(stream)
+    e1.synchronize()
+    sp_us = e0.elapsed_time(e1) * 1e3 / reps
+    sp_bytes = 6 * nnz + 4 * n + 4 * n
+    spmv = {"achieved": sp_bytes / (sp_us * 1e-6) / 1e9, "avg_launch_us": sp_us, "unit": "GB/s",
+            "algorithmic_bytes_per_launch": sp_bytes}
+    spmv["frac"] = spmv["achieved"] / hbm
+
+    # ---- comparators on the same GPU (one solve each)
+    comparators = {}
+    if not args.no_comparators:
+        for kind in ("fp32-F3R", "fgmres64"):
+            cp = f3r.preset(kind, diag_scale=ds)
+            sc = f3r.Solver(rp, ci, va, cp, stream=stream)
+            xc = torch.zeros(n, dtype=torch.float64, device=dev)
+            sc.solve(b, xc, stream=stream)  # warm-up (graphs, clocks)
+            xc.zero_()
+            flush.fill_(3.0)
+            e0.record(stream)
+            rc = sc.solve(b, xc, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            comparators[kind] = {"ms": e0.elapsed_time(e1), "outer_iters": rc.outer_iters,
+                                 "status": f3r.STATUS.get(rc.status), "rel_res": rc.rel_res_true}
+            sc.close()
+            del xc
+        comparators["speedup_vs_fgmres64"] = comparators["fgmres64"]["ms"] / ms_per_solve
+        comparators["speedup_vs_fp32_f3r"] = comparators["fp32-F3R"]["ms"] / ms_per_solve
+
+    # ---- end to end through the C ABI with host buffers (setup + solve + result)
+    rp_h = torch.from_numpy(prob.rowptr).pin_memory()
+    ci_h = torch.from_numpy(prob.colidx).pin_memory()
+    va_h = torch.from_numpy(prob.val).pin_memory()
+    b_h = torch.from_numpy(prob.b).pin_memory()
+    x_h = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for it in range(1 + args.e2e_steps):
+        x_h.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        se = f3r.Solver(rp_h, ci_h, va_h, prm)
+        se.solve(b_h, x_h)
+        se.close()
+        torch.cuda.synchronize()
+        if it > 0:
+            e2e_times.append((time.perf_counter() - t0) * 1e3)
+    e2e = {"value": statistics.median(e2e_times) / ws, "unit": "ms",
+           "h2d_bytes_per_step": int(4 * (n + 1) + 12 * nnz + 16 * n), "d2h_bytes_per_step": int(8 * n),
+           "what": "f3r_setup from pinned host CSR + f3r_solve with host b/x + result copied back"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload], "solver": args.kind,
+                   "n": n, "nnz": nnz, "tol": 1e-9, "parallelism": "replicas" if ws > 1 else "1 gpu",
+                   "l2": "flushed (256 MiB write) before every timed solve"},
+        "outer_iters": last.outer_iters, "rel_res_true": true_rel, "status": f3r.STATUS.get(last.status),
+        "roofline": roofline, "spmv_fp16": spmv, "kernels": prof, "comparators": comparators,
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        "device_bytes": s.device_bytes,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob, args.kind, last.outer_iters)
+    if rank == 0:
+        print(json.dumps(out))
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * f3r.h -- C ABI of libf3r.so, a GB300 (sm_103a) implementation of the F3R
+ * nested Krylov solver for sparse A x = b from "A Nested Krylov Method Using
+ * Half-Precision Arithmetic" (arXiv 2505.20719).
+ *
+ * F3R = (F_{m1}, F_{m2}, F_{m3}, R_{m4}, M): an fp64 flexible GMRES whose
+ * preconditioner is an fp32 FGMRES, preconditioned by an FGMRES with fp16 A
+ * and fp32 vectors, preconditioned by an fp16 Richardson iteration with
+ * adaptive weights, preconditioned by the primary preconditioner M
+ * (Sec. 3 tuple notation; Sec. 4.2; Table 1; Algorithm 1; Eqs. 4-5).
+ *
+ * Conventions for every entry point:
+ *  - Pointers may be host memory (pageable or pinned) or device memory of
+ *    the current device; the library tells them apart with
+ *    cudaPointerGetAttributes and copies host data itself.  The caller owns
+ *    every pointer it passes; setup copies what it keeps.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  All device work of a call is ordered on that stream.
+ *  - Indices are 0-based int32 (Sec. 5: 32-bit column indices and row
+ *    pointers); rowptr has n+1 monotone entries, 0 <= colidx < n.
+ *  - Errors are returned as f3r_status; nothing aborts the process and no
+ *    kernel traps.  After F3R_ERR_CUDA the context should be destroyed.
+ *  - One context is used by one host thread at a time.  There is no CPU
+ *    fallback: without a usable GPU every call returns F3R_ERR_CUDA.
+ *
+ * Precision codes (Table 1): 0 = fp64, 1 = fp32, 2 = fp16 (binary16),
+ * 3 = bf16 (bfloat16, with power-of-two per-row scaling of A).
+ */
+#ifndef F3R_H
+#define F3R_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct f3r_ctx f3r_ctx;
+
+typedef enum {
+    F3R_OK = 0,
+    F3R_ERR_ARG = 1,          /* invalid argument or matrix (bad rowptr/colidx, n <= 0, ...) */
+    F3R_ERR_CUDA = 2,         /* a CUDA call failed or no device is usable */
+    F3R_ERR_NOMEM = 3,        /* device or pinned host allocation failed */
+    F3R_NOT_CONVERGED = 4,    /* max_outer reached; x holds the last iterate */
+    F3R_ERR_BREAKDOWN = 5,    /* reserved */
+    F3R_ERR_NONFINITE = 6,    /* a non-finite value reached the outer fp64 level */
+    F3R_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+    F3R_ERR_UNSUPPORTED = 8   /* parameter combination not built */
+} f3r_status;
+
+enum { F3R_F64 = 0, F3R_F32 = 1, F3R_F16 = 2, F3R_BF16 = 3 };
+enum { F3R_PC_IDENTITY = 0, F3R_PC_JACOBI = 1 };
+
+/* Solver configuration.  f3r_default_params gives F3R with the paper's
+ * defaults: (m1, m2, m3, m4) = (100, 8, 4, 2), c = 64, Table 1 precisions,
+ * Jacobi M, CGS2, tolerance 1e-9, 300 outer iterations at most. */
+typedef struct {
+    int nlevels;        /* FGMRES levels 1..4; level 0 is the outer fp64 FGMRES on the original A */
+    int m[4];           /* iterations per FGMRES level; m[0] is the restart length m1 (<= 128),
+                           inner levels <= 15 */
+    int a_prec[4];      /* precision of A used by each level; a_prec[0] must be F3R_F64 */
+    int v_prec[4];      /* vector precision per level: F3R_F64 or F3R_F32 (v_prec[0] = F3R_F64) */
+    int rich_m;         /* Richardson iterations m4 (0 = the innermost FGMRES applies M), <= 8 */
+    int rich_a_prec;    /* precision of A inside Richardson */
+    int rich_v_prec;    /* precision of Richardson vectors: F16, BF16, F32 or F64 */
+    int m_prec;         /* storage precision of M */
+    int precond;        /* F3R_PC_JACOBI (M = diag(A^)^-1) or F3R_PC_IDENTITY */
+    int c;              /* weight-update period of Algorithm 1 (>= 1) */
+    double omega_fixed; /* > 0: fixed Richardson weight, no adaptive update */
+    int diag_scale;     /* 1: inner nest works on A^ = D^-1/2 A D^-1/2, D = |diag A| (Sec. 5) */
+    int row_scale;      /* 1: power-of-two row scaling of 16-bit copies of A */
+    int scale_cast;     /* 1: power-of-two scaling of vectors cast into 16-bit storage */
+    int cgs_passes;     /* 1 = classical Gram-Schmidt (Sec. 4.2), 2 = CGS2 */
+    double tol;         /* target ||b - A x||_2 / ||b||_2 */
+    int max_outer;      /* total outer iterations before F3R_NOT_CONVERGED (Sec. 5: 300) */
+    int use_graphs;     /* 1: replay each outer iteration as one CUDA graph */
+    int keep_omega;     /* 1: keep the Richardson weights and counter of the previous solve */
+    int reserved[7];
+} f3r_params;
+
+typedef struct {
+    int status;            /* f3r_status of the solve */
+    int outer_iters;       /* outer (F_{m1}) iterations over all restarts */
+    int restarts;          /* number of restarts of the whole nest */
+    double rel_res_true;   /* final fp64 ||b - A x|| / ||b|| */
+    int64_t m_applies;     /* applications of M (Sec. 4.2: 64 per outer iteration) */
+    int64_t r_calls;       /* Richardson calls */
+    int64_t r_update_calls;/* Richardson calls that computed w' (every c-th) */
+    double omega[8];       /* Richardson weights at exit */
+    double *hist;          /* caller-owned host array: |g_{j+1}|/||b|| per outer iteration */
+    int hist_cap;
+    int hist_len;
+    double *true_hist;     /* caller-owned host array: true residual at each cycle start and exit */
+    int true_cap;
+    int true_len;
+    double t_solve_ms;     /* device time of the solve (CUDA events) */
+    int64_t kernel_launches; /* kernels launched by the solve (graph nodes included) */
+    int64_t graph_launches;
+} f3r_stats;
+
+/* Fill *p with the paper's F3R defaults (Sec. 4.2, Sec. 5, Table 1). */
+f3r_status f3r_default_params(f3r_params *p);
+
+/* Build a solver for the n x n CSR matrix (rowptr, colidx, val; host or
+ * device pointers, fp64 values): validates the matrix, applies the diagonal
+ * scaling of Sec. 5, converts A to sliced ELLPACK with slices of 32 rows
+ * (Sec. 5.2) and stores the fp64 / fp32 / fp16 / bf16 copies the levels use
+ * (Table 1), allocates all workspace.  *ctx is written on success.
+ * Errors: F3R_ERR_ARG (bad matrix or parameters), F3R_ERR_NOMEM, F3R_ERR_CUDA. */
+f3r_status f3r_setup(f3r_ctx **ctx, int32_t n, int64_t nnz, const int32_t *rowptr,
+                     const int32_t *colidx, const double *val, const f3r_params *params,
+                     void *stream);
+
+/* Solve A x = b (b, x: n fp64 values, host or device).  x holds the initial
+ * guess on entry (Sec. 5 uses x0 = 0) and the solution on exit.  Returns
+ * F3R_OK when ||b - A x|| / ||b|| < tol, F3R_NOT_CONVERGED after max_outer
+ * outer iterations (x = last iterate), F3R_ERR_NONFINITE if a non-finite
+ * value reaches the outer level.  `stats` may be NULL.  Synchronises the
+ * stream once per outer iteration to read the convergence estimate. */
+f3r_status f3r_solve(f3r_ctx *ctx, const double *b, double *x, f3r_stats *stats, void *stream);
+
+/* y = A_p x with A_p the precision-p copy of the scaled matrix (p = 0
+ * returns the original fp64 A).  x and y are device pointers of vector
+ * precision vp: fp64 for p = 0, else vp = F3R_F32 (y fp32, row sums in
+ * fp32) or vp = F3R_F16 / F3R_BF16 (x 16-bit, y fp32).  Row sums use
+ * fused multiply-add in CSR order.  Errors: F3R_ERR_ARG if the context
+ * holds no copy in precision p. */
+f3r_status f3r_spmv(f3r_ctx *ctx, int p, int vp, const void *x, void *y, void *stream);
+
+/* One preconditioner application at nesting depth `level` with the current
+ * Richardson state (test and instrumentation entry):
+ *   1 <= level < nlevels : one call of inner FGMRES level `level`, x and z in
+ *                          that level's vector precision;
+ *   level == nlevels     : one Richardson call (Algorithm 1), or M if
+ *                          rich_m = 0; x and z in the vector precision of
+ *                          level nlevels-1.
+ * x and z are device pointers of n elements. */
+f3r_status f3r_apply(f3r_ctx *ctx, int level, const void *x, void *z, void *stream);
+
+/* Read / write the Richardson state (omega[0..m4-1], call counter c_ntr). */
+f3r_status f3r_get_rich_state(f3r_ctx *ctx, double *omega8, int64_t *c_ntr);
+f3r_status f3r_set_rich_state(f3r_ctx *ctx, const double *omega8, int64_t c_ntr);
+
+/* Copy a set-up array back to host memory `out` in CSR order (test entry):
+ * 0 d = D^-1/2 (double, n); 1 A^ fp64 (nnz); 2 A^ fp32 (float, nnz);
+ * 3 A^/s fp16 (uint16 bits, nnz); 4 A^/s bf16 (uint16 bits, nnz);
+ * 5 row scales (float, n); 6 M in m_prec (n elements of that precision).
+ * Returns F3R_ERR_ARG if the array does not exist. */
+f3r_status f3r_export(f3r_ctx *ctx, int which, void *out);
+
+/* Kernel event profiler (instrumentation).  With enable = 1 the totals are
+ * reset, every kernel the context launches is bracketed by two CUDA events
+ * on its launching stream, and solves run without graph replay.  Slot s
+ * aggregates one kernel kind at one nesting level: kind = s / 4, level =
+ * s % 4; f3r_profile_slot_name(s) names the kind.  f3r_profile_get returns
+ * the number of timed launches and their summed device time (ms). */
+f3r_status f3r_profile_enable(f3r_ctx *ctx, int enable);
+f3r_status f3r_profile_get(f3r_ctx *ctx, int slot, int64_t *launches, double *total_ms);
+int f3r_profile_slots(void);
+const char *f3r_profile_slot_name(int slot);
+
+/* Device memory held by the context, in bytes. */
+int64_t f3r_device_bytes(const f3r_ctx *ctx);
+
+void f3r_destroy(f3r_ctx *ctx);
+const char *f3r_status_str(f3r_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* F3R_H */

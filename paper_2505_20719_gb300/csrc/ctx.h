@@ -1,0 +1,154 @@
+// Host-side state of one solver context and the launchers shared by the
+// translation units of libf3r.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace f3r {
+
+struct LevelHost {
+    int m = 0, a_prec = 0, v_prec = 0, child = 2;
+    void *V = nullptr, *Z = nullptr, *w = nullptr, *scal = nullptr;
+};
+
+// What the host reads back after every outer iteration (pinned memory).
+struct Readback {
+    double est;       // |g_{j+1}| / ||b||
+    double rel;       // true relative residual at a cycle start
+    double nb;        // ||b||
+    int flags[16];    // copy of all levels' flags
+    unsigned long long counters[4];
+};
+
+// Where an FGMRES level writes its result z.
+struct OutSlot {
+    void *ptr = nullptr;    // vector of type out_prec
+    int prec = F3R_F32;
+    bool dscale = false;    // multiply by D^-1/2 (return to the outer level)
+};
+
+// Kernel timing slots (kind * 4 + level) for the event profiler.
+enum {
+    PK_SPMV_DOTS = 0, PK_CGS_PASS, PK_CGS_FINAL, PK_NORMALIZE, PK_COMBINE, PK_START, PK_M, PK_RICH2,
+    PK_RICH_STEP, PK_RICH_UPD, PK_OUTER_SPMV, PK_OUTER_CGS, PK_OUTER_OTHER, PK_SPMV, PK_KINDS
+};
+constexpr int kProfSlots = PK_KINDS * 4;
+
+struct ProfRec {
+    int slot;
+    cudaEvent_t a, b;
+};
+
+struct Ctx {
+    int dev = 0, nsm = 0;
+    f3r_params prm{};
+    int n = 0;
+    long long nnz = 0;
+    int ld = 0;            // stride between vectors of a basis
+    // sliced ELLPACK (slices of 32 rows, column-major inside a slice)
+    int nslices = 0;
+    long long nsell = 0;
+    int *sptr = nullptr, *col = nullptr, *rowptr = nullptr;
+    double *a64 = nullptr;      // original A
+    double *ah64 = nullptr;     // scaled A^ in fp64
+    float *a32 = nullptr;       // A^ in fp32
+    h16 *a16 = nullptr;         // A^ / s in fp16
+    b16 *abf = nullptr;         // A^ / s in bf16
+    float *rs = nullptr;        // power-of-two row scales s (row_scale = 1)
+    double *dsc = nullptr;      // D^-1/2
+    void *mvec = nullptr;       // M in m_prec
+    LevelHost L[4];
+    // Richardson
+    void *rin = nullptr, *rz[2] = {nullptr, nullptr}, *rr = nullptr;
+    void *omega = nullptr, *wcur = nullptr;
+    unsigned long long *counters = nullptr;
+    long long *c_ntr_base = nullptr;
+    long long c_ntr = 1;
+    double omega_host[kMaxRich];
+    int calls_per_outer = 0;
+    // reductions and flags
+    void *partials = nullptr;
+    unsigned *ticket = nullptr;
+    int G = 1, Gs = 1, G1 = 1;
+    int *flags = nullptr;       // 4 ints per level
+    int *jdev = nullptr;
+    void *zst = nullptr;        // the outer level's preconditioner output (fp64)
+    void *apply_misc = nullptr; // scalars of a stand-alone Richardson call
+    double *bdev = nullptr, *xdev = nullptr;
+    Readback *rb = nullptr;     // pinned
+    double *hostval = nullptr;  // pinned scratch
+    std::map<long long, cudaGraphExec_t> graphs;
+    long long launches = 0, graph_launches = 0;
+    long long launches_per_graph_iter = 0;
+    long long bytes = 0;
+    std::vector<void *> allocs;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // event profiler: when on, every launch is bracketed by two events on its stream
+    bool prof = false;
+    std::vector<ProfRec> prec;
+    size_t prec_used = 0;
+    double prof_ms[kProfSlots] = {};
+    long long prof_cnt[kProfSlots] = {};
+};
+
+inline void prof_begin(Ctx &c, int kind, int level, cudaStream_t s) {
+    if (!c.prof) return;
+    if (c.prec_used == c.prec.size()) {
+        ProfRec r;
+        cudaEventCreate(&r.a);
+        cudaEventCreate(&r.b);
+        c.prec.push_back(r);
+    }
+    ProfRec &r = c.prec[c.prec_used];
+    r.slot = kind * 4 + (level & 3);
+    cudaEventRecord(r.a, s);
+}
+inline void prof_end(Ctx &c, cudaStream_t s) {
+    if (!c.prof) return;
+    cudaEventRecord(c.prec[c.prec_used].b, s);
+    c.prec_used++;
+}
+// after a synchronisation: fold the recorded pairs into the per-slot totals
+inline void prof_collect(Ctx &c) {
+    for (size_t i = 0; i < c.prec_used; ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c.prec[i].a, c.prec[i].b) == cudaSuccess) {
+            c.prof_ms[c.prec[i].slot] += ms;
+            c.prof_cnt[c.prec[i].slot] += 1;
+        }
+    }
+    c.prec_used = 0;
+}
+
+inline Sell sell_of(const Ctx &c) { return Sell{c.n, c.nslices, c.sptr, c.col}; }
+
+// setup.cu
+f3r_status build_matrix(Ctx &c, const int *rowptr_d, const int *colidx_d, const double *val_d, cudaStream_t s);
+f3r_status export_array(Ctx &c, int which, void *out, cudaStream_t s);
+
+// launch_levels.cu
+void launch_level_start(Ctx &c, int d, const void *x, cudaStream_t s);
+void launch_normalize(Ctx &c, int d, bool from_w, int dst, cudaStream_t s);
+void launch_spmv_dots(Ctx &c, int d, int j, cudaStream_t s);
+void launch_cgs_pass(Ctx &c, int d, int j, cudaStream_t s);
+void launch_cgs_final(Ctx &c, int d, int j, bool last, cudaStream_t s);
+void launch_combine(Ctx &c, int d, const OutSlot &o, cudaStream_t s);
+void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s);
+void launch_outer_residual(Ctx &c, const double *b, const double *x, bool compute_nb, cudaStream_t s);
+void launch_outer_step(Ctx &c, cudaStream_t s);
+void launch_outer_finish(Ctx &c, double *x, cudaStream_t s);
+void launch_advance(Ctx &c, long long inc, cudaStream_t s);
+f3r_status launch_spmv(Ctx &c, int p, int vp, const void *x, void *y, cudaStream_t s);
+
+// launch_rich.cu
+void launch_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s);
+void launch_rich_prep(Ctx &c, const void *x, cudaStream_t s);
+
+// sizes
+int prec_bytes(int p);
+
+}  // namespace f3r

@@ -1,0 +1,338 @@
+// Launchers of the FGMRES-level kernels, dispatching on the precisions of
+// each level (Table 1).
+#include "ctx.h"
+#include "kernels.cuh"
+
+namespace f3r {
+
+template <class T> static LevelDev<T> levdev(Ctx &c, int d) {
+    LevelDev<T> L;
+    L.n = c.n;
+    L.ld = c.ld;
+    L.m = c.L[d].m;
+    L.depth = d;
+    L.V = (T *)c.L[d].V;
+    L.Z = (T *)c.L[d].Z;
+    L.w = (T *)c.L[d].w;
+    L.scal = (T *)c.L[d].scal;
+    L.flags = c.flags;
+    L.jptr = (d == 0) ? c.jdev : nullptr;
+    return L;
+}
+
+template <class T> static GridRed<T> gred(Ctx &c, int stride) {
+    return GridRed<T>{(T *)c.partials, c.ticket, stride};
+}
+
+static bool rich_half(const Ctx &c) {
+    return c.prm.rich_m > 0 && (c.prm.rich_v_prec == F3R_F16 || c.prm.rich_v_prec == F3R_BF16);
+}
+
+// the level below d wants the 16-bit cast scale of V[j+1]
+static int want_sigma(const Ctx &c, int d) {
+    return (c.L[d].child == CHILD_R && rich_half(c) && c.prm.scale_cast) ? 1 : 0;
+}
+
+// ------------------------------------------------------------------ start
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_level_start(const T *x, LevelDev<T> C, int want_sig, GridRed<T> gr) {
+    T acc[2] = {(T)0, (T)0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C.n; i += gridDim.x * blockDim.x) {
+        const T v = x[i];
+        C.V[i] = v;
+        acc[0] = fma_rn(v, v, acc[0]);
+        acc[1] = fmax(acc[1], fabs(v));
+    }
+    grid_reduce<T, 2>(acc, 1, true, gr, [&](T *res) {
+        T *ms = C.misc();
+        int *cf = C.fl();
+        const T beta = sqrt_rn(res[0]);
+        cf[IF_KDIM] = 0;
+        cf[IF_NONFINITE] = isfinite(beta) ? 0 : 1;
+        const bool run = (beta > (T)0) && isfinite(beta);
+        cf[IF_STOP] = run ? 0 : 1;
+        ms[MS_BETA] = beta;
+        if (run) {
+            ms[MS_INV] = div_rn((T)1, beta);
+            C.g()[0] = beta;
+            const T sg = want_sig ? pow2_scale_for(mul_rn(res[1], ms[MS_INV])) : (T)1;
+            ms[MS_SIGMA] = sg;
+            ms[MS_INV_SIGMA] = div_rn((T)1, sg);
+        }
+    });
+}
+
+void launch_level_start(Ctx &c, int d, const void *x, cudaStream_t s) {
+    prof_begin(c, PK_START, d, s);
+    if (c.L[d].v_prec == F3R_F64)
+        k_level_start<double><<<c.G, kBlock, 0, s>>>((const double *)x, levdev<double>(c, d), want_sigma(c, d),
+                                                      gred<double>(c, kMaxDots));
+    else
+        k_level_start<float><<<c.G, kBlock, 0, s>>>((const float *)x, levdev<float>(c, d), want_sigma(c, d),
+                                                     gred<float>(c, kMaxDots));
+    prof_end(c, s);
+    c.launches++;
+}
+
+// -------------------------------------------------------------- normalise
+template <class T, class TC, int CHILD>
+static void norm_go(Ctx &c, int d, bool from_w, int dst, cudaStream_t s) {
+    LevelDev<T> L = levdev<T>(c, d);
+    ChildOut<TC> co{};
+    if (CHILD == CHILD_F) {
+        co.x = (TC *)c.L[d + 1].V;
+        co.dsc = (d == 0 && c.prm.diag_scale) ? c.dsc : nullptr;
+        co.cscal = c.L[d + 1].scal;
+        co.cm = c.L[d + 1].m;
+        co.cdepth = d + 1;
+        co.want_sigma = want_sigma(c, d + 1);
+    } else if (CHILD == CHILD_R) {
+        co.x = (TC *)c.rin;
+    }
+    const T *src = from_w ? L.w : L.V;  // at a level start V[0] is normalised in place
+    // V[0] of the outer level is addressed through j (= 0 at a cycle start)
+    prof_begin(c, PK_NORMALIZE, d, s);
+    k_normalize<T, TC, CHILD><<<c.G, kBlock, 0, s>>>(L, src, dst, d, co, gred<T>(c, kMaxDots));
+    prof_end(c, s);
+    c.launches++;
+}
+
+void launch_normalize(Ctx &c, int d, bool from_w, int dst, cudaStream_t s) {
+    const bool t64 = c.L[d].v_prec == F3R_F64;
+    const int ch = c.L[d].child;
+    if (ch == CHILD_F) {
+        const bool c64 = c.L[d + 1].v_prec == F3R_F64;
+        if (t64 && c64) norm_go<double, double, CHILD_F>(c, d, from_w, dst, s);
+        else if (t64) norm_go<double, float, CHILD_F>(c, d, from_w, dst, s);
+        else if (c64) norm_go<float, double, CHILD_F>(c, d, from_w, dst, s);
+        else norm_go<float, float, CHILD_F>(c, d, from_w, dst, s);
+    } else if (ch == CHILD_R) {
+        switch (c.prm.rich_v_prec) {
+            case F3R_F64: norm_go<double, double, CHILD_R>(c, d, from_w, dst, s); break;
+            case F3R_F32:
+                if (t64) norm_go<double, float, CHILD_R>(c, d, from_w, dst, s);
+                else norm_go<float, float, CHILD_R>(c, d, from_w, dst, s);
+                break;
+            case F3R_F16:
+                if (t64) norm_go<double, h16, CHILD_R>(c, d, from_w, dst, s);
+                else norm_go<float, h16, CHILD_R>(c, d, from_w, dst, s);
+                break;
+            default:
+                if (t64) norm_go<double, b16, CHILD_R>(c, d, from_w, dst, s);
+                else norm_go<float, b16, CHILD_R>(c, d, from_w, dst, s);
+                break;
+        }
+    } else {
+        if (t64) norm_go<double, double, CHILD_M>(c, d, from_w, dst, s);
+        else norm_go<float, float, CHILD_M>(c, d, from_w, dst, s);
+    }
+}
+
+// ------------------------------------------------------------ SpMV + dots
+void launch_spmv_dots(Ctx &c, int d, int j, cudaStream_t s) {
+    const Sell S = sell_of(c);
+    const float *rs = c.prm.row_scale ? c.rs : nullptr;
+    prof_begin(c, PK_SPMV_DOTS, d, s);
+    if (c.L[d].v_prec == F3R_F64) {
+        k_spmv_dots<double, double><<<c.Gs, kBlock, 0, s>>>(S, c.ah64, nullptr, levdev<double>(c, d), j,
+                                                             gred<double>(c, kMaxDots));
+    } else {
+        switch (c.L[d].a_prec) {
+            case F3R_F32:
+                k_spmv_dots<float, float><<<c.Gs, kBlock, 0, s>>>(S, c.a32, nullptr, levdev<float>(c, d), j,
+                                                                  gred<float>(c, kMaxDots));
+                break;
+            case F3R_F16:
+                k_spmv_dots<h16, float><<<c.Gs, kBlock, 0, s>>>(S, c.a16, rs, levdev<float>(c, d), j,
+                                                                gred<float>(c, kMaxDots));
+                break;
+            default:
+                k_spmv_dots<b16, float><<<c.Gs, kBlock, 0, s>>>(S, c.abf, rs, levdev<float>(c, d), j,
+                                                                gred<float>(c, kMaxDots));
+                break;
+        }
+    }
+    prof_end(c, s);
+    c.launches++;
+}
+
+void launch_cgs_pass(Ctx &c, int d, int j, cudaStream_t s) {
+    prof_begin(c, PK_CGS_PASS, d, s);
+    if (c.L[d].v_prec == F3R_F64)
+        k_cgs_pass<double><<<c.G, kBlock, 0, s>>>(levdev<double>(c, d), j, gred<double>(c, kMaxDots));
+    else
+        k_cgs_pass<float><<<c.G, kBlock, 0, s>>>(levdev<float>(c, d), j, gred<float>(c, kMaxDots));
+    prof_end(c, s);
+    c.launches++;
+}
+
+void launch_cgs_final(Ctx &c, int d, int j, bool last, cudaStream_t s) {
+    const int ws = want_sigma(c, d);
+    prof_begin(c, PK_CGS_FINAL, d, s);
+    if (c.L[d].v_prec == F3R_F64)
+        k_cgs_final<double><<<c.G, kBlock, 0, s>>>(levdev<double>(c, d), j, c.prm.cgs_passes, last ? 1 : 0, ws,
+                                                    gred<double>(c, kMaxDots));
+    else
+        k_cgs_final<float><<<c.G, kBlock, 0, s>>>(levdev<float>(c, d), j, c.prm.cgs_passes, last ? 1 : 0, ws,
+                                                   gred<float>(c, kMaxDots));
+    prof_end(c, s);
+    c.launches++;
+}
+
+// --------------------------------------------------------------- combine
+template <class T, class TP>
+static void comb_go(Ctx &c, int d, const OutSlot &o, cudaStream_t s) {
+    prof_begin(c, PK_COMBINE, d, s);
+    k_combine<T, TP><<<c.G, kBlock, 0, s>>>(levdev<T>(c, d), (TP *)o.ptr, nullptr, 0, o.dscale ? c.dsc : nullptr);
+    prof_end(c, s);
+    c.launches++;
+}
+
+void launch_combine(Ctx &c, int d, const OutSlot &o, cudaStream_t s) {
+    const bool t64 = c.L[d].v_prec == F3R_F64;
+    const bool p64 = o.prec == F3R_F64;
+    if (t64 && p64) comb_go<double, double>(c, d, o, s);
+    else if (t64) comb_go<double, float>(c, d, o, s);
+    else if (p64) comb_go<float, double>(c, d, o, s);
+    else comb_go<float, float>(c, d, o, s);
+}
+
+// -------------------------------------------------------------------- M
+void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s) {
+    (void)j;
+    const bool t64 = c.L[d].v_prec == F3R_F64;
+    unsigned long long *cnt = c.counters;
+    const int n = c.n;
+    const int *ij = use_j ? c.jdev : nullptr;
+    prof_begin(c, PK_M, d, s);
+    if (t64) {
+        switch (c.prm.m_prec) {
+            case F3R_F64: k_apply_M<double, double><<<c.G, kBlock, 0, s>>>((const double *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F32: k_apply_M<double, float><<<c.G, kBlock, 0, s>>>((const float *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F16: k_apply_M<double, h16><<<c.G, kBlock, 0, s>>>((const h16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            default: k_apply_M<double, b16><<<c.G, kBlock, 0, s>>>((const b16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+        }
+    } else {
+        switch (c.prm.m_prec) {
+            case F3R_F32: k_apply_M<float, float><<<c.G, kBlock, 0, s>>>((const float *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F16: k_apply_M<float, h16><<<c.G, kBlock, 0, s>>>((const h16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_BF16: k_apply_M<float, b16><<<c.G, kBlock, 0, s>>>((const b16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            default: k_apply_M<float, double><<<c.G, kBlock, 0, s>>>((const double *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+        }
+    }
+    prof_end(c, s);
+    c.launches++;
+}
+
+// ------------------------------------------------------------ outer level
+void launch_outer_residual(Ctx &c, const double *b, const double *x, bool compute_nb, cudaStream_t s) {
+    prof_begin(c, PK_OUTER_OTHER, 0, s);
+    k_outer_residual<<<c.Gs, kBlock, 0, s>>>(sell_of(c), c.a64, b, x, levdev<double>(c, 0), gred<double>(c, kMaxDots),
+                                              compute_nb ? 1 : 0);
+    prof_end(c, s);
+    c.launches++;
+}
+
+// w = A z (z = the inner nest's output), Z[j] = z, CGS2, Givens, estimate
+__global__ void __launch_bounds__(kBlock) k_outer_store_z(LevelDev<double> L, const double *z) {
+    const int j = *L.jptr;
+    double *dst = L.Z + (size_t)j * L.ld;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) dst[i] = z[i];
+}
+
+void launch_outer_step(Ctx &c, cudaStream_t s) {
+    LevelDev<double> L = levdev<double>(c, 0);
+    prof_begin(c, PK_OUTER_SPMV, 0, s);
+    k_outer_store_z<<<c.G, kBlock, 0, s>>>(L, (const double *)c.zst);
+    k_outer_spmv<<<c.Gs, kBlock, 0, s>>>(sell_of(c), c.a64, L);
+    prof_end(c, s);
+    double *part = (double *)c.partials;
+    prof_begin(c, PK_OUTER_CGS, 0, s);
+    k_outer_cgs<0><<<c.G1, 512, 0, s>>>(L, c.prm.cgs_passes, part, c.ticket);
+    c.launches += 3;
+    if (c.prm.cgs_passes == 2) {
+        k_outer_cgs<1><<<c.G1, 512, 0, s>>>(L, c.prm.cgs_passes, part, c.ticket);
+        c.launches++;
+    }
+    k_outer_cgs<2><<<c.G1, 512, 0, s>>>(L, c.prm.cgs_passes, part, c.ticket);
+    prof_end(c, s);
+    c.launches++;
+}
+
+void launch_outer_finish(Ctx &c, double *x, cudaStream_t s) {
+    LevelDev<double> L = levdev<double>(c, 0);
+    prof_begin(c, PK_OUTER_OTHER, 0, s);
+    k_outer_solve_y<<<1, 32, 0, s>>>(L);
+    k_outer_update_x<<<c.G, kBlock, 0, s>>>(L, x);
+    prof_end(c, s);
+    c.launches += 2;
+}
+
+__global__ void k_advance(long long *p, long long inc) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p += inc;
+}
+
+void launch_advance(Ctx &c, long long inc, cudaStream_t s) {
+    prof_begin(c, PK_OUTER_OTHER, 0, s);
+    k_advance<<<1, 32, 0, s>>>(c.c_ntr_base, inc);
+    prof_end(c, s);
+    c.launches++;
+}
+
+// ------------------------------------------------------- stand-alone SpMV
+template <class TA, class TX, class TY>
+__global__ void __launch_bounds__(kBlock) k_spmv(Sell S, const TA *__restrict__ val, const float *__restrict__ rs,
+                                                 const TX *__restrict__ x, TY *y) {
+    const int lane = threadIdx.x & 31;
+    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int s = wid; s < S.nslices; s += nw) {
+        TY acc = sell_row<TY>(S, val, s, lane, [&](int c) { return to_c<TY>(__ldg(x + c)); });
+        const int i = s * kSlice + lane;
+        if (rs) acc = mul_rn(acc, (TY)__ldg(rs + i));
+        if (i < S.n) y[i] = acc;
+    }
+}
+
+f3r_status launch_spmv(Ctx &c, int p, int vp, const void *x, void *y, cudaStream_t s) {
+    const Sell S = sell_of(c);
+    const float *rs = c.prm.row_scale ? c.rs : nullptr;
+    const int g = c.Gs;
+    prof_begin(c, PK_SPMV, p, s);
+    switch (p) {
+        case F3R_F64:
+            if (vp != F3R_F64) return F3R_ERR_ARG;
+            k_spmv<double, double, double><<<g, kBlock, 0, s>>>(S, c.a64, nullptr, (const double *)x, (double *)y);
+            break;
+        case F3R_F32:
+            if (!c.a32 || vp != F3R_F32) return F3R_ERR_ARG;
+            k_spmv<float, float, float><<<g, kBlock, 0, s>>>(S, c.a32, nullptr, (const float *)x, (float *)y);
+            break;
+        case F3R_F16:
+            if (!c.a16) return F3R_ERR_ARG;
+            if (vp == F3R_F32)
+                k_spmv<h16, float, float><<<g, kBlock, 0, s>>>(S, c.a16, rs, (const float *)x, (float *)y);
+            else if (vp == F3R_F16)
+                k_spmv<h16, h16, float><<<g, kBlock, 0, s>>>(S, c.a16, rs, (const h16 *)x, (float *)y);
+            else
+                return F3R_ERR_ARG;
+            break;
+        case F3R_BF16:
+            if (!c.abf) return F3R_ERR_ARG;
+            if (vp == F3R_F32)
+                k_spmv<b16, float, float><<<g, kBlock, 0, s>>>(S, c.abf, rs, (const float *)x, (float *)y);
+            else if (vp == F3R_BF16)
+                k_spmv<b16, b16, float><<<g, kBlock, 0, s>>>(S, c.abf, rs, (const b16 *)x, (float *)y);
+            else
+                return F3R_ERR_ARG;
+            break;
+        default:
+            prof_end(c, s);
+            return F3R_ERR_ARG;
+    }
+    prof_end(c, s);
+    c.launches++;
+    return F3R_OK;
+}
+
+}  // namespace f3r

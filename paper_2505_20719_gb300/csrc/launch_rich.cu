@@ -1,0 +1,104 @@
+// Launchers of the Richardson level (Algorithm 1), dispatching on the
+// storage of A and of the Richardson vectors.
+#include "ctx.h"
+#include "rich.cuh"
+
+namespace f3r {
+
+template <class TC> static RichDev<TC> richdev(Ctx &c) {
+    return RichDev<TC>{(TC *)c.omega, (TC *)c.wcur, c.counters, c.c_ntr_base};
+}
+
+template <class TA, class VS, class TC, class TP>
+static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const TP *par_misc, cudaStream_t s) {
+    const Sell S = sell_of(c);
+    const float *rs = (c.prm.row_scale && IsHalfWidth<TA>::value) ? c.rs : nullptr;
+    const VS *v = (const VS *)c.rin;
+    const VS *mv = (const VS *)c.mvec;
+    const int m4 = c.prm.rich_m, n = c.n;
+    const int cd = c.prm.nlevels - 1;
+    RichDev<TC> R = richdev<TC>(c);
+    VS *zb[2] = {(VS *)c.rz[0], (VS *)c.rz[1]};
+    if (!update) {
+        if (m4 == 2) {
+            prof_begin(c, PK_RICH2, 0, s);
+            k_rich2<TA, VS, TC, TP><<<c.Gs, kBlock, 0, s>>>(S, val, rs, v, mv, out, par_misc, R, c.flags, cd, n);
+            prof_end(c, s);
+            c.launches++;
+        } else {
+            for (int k = 0; k < m4; ++k) {
+                const bool last = (k == m4 - 1);
+                const VS *zp = (k > 0) ? zb[(k - 1) & 1] : nullptr;
+                prof_begin(c, PK_RICH_STEP, 0, s);
+                k_rich_step<TA, VS, TC, TP><<<c.Gs, kBlock, 0, s>>>(S, val, rs, v, mv, zp, zb[k & 1], out, par_misc,
+                                                                    R, k, last ? 1 : 0, c.flags, cd, n);
+                prof_end(c, s);
+                c.launches++;
+            }
+        }
+        return;
+    }
+    // update call: every step computes w'_k (Algorithm 1, update branch)
+    VS *r = (VS *)c.rr;
+    GridRed<TC> gr{(TC *)c.partials, c.ticket, kMaxDots};
+    for (int k = 0; k < m4; ++k) {
+        const bool last = (k == m4 - 1);
+        const VS *zp = (k > 0) ? zb[(k - 1) & 1] : nullptr;
+        const VS *rk = v;  // r_0 = v without an SpMV
+        prof_begin(c, PK_RICH_UPD, 0, s);
+        if (k > 0) {
+            k_rich_upd_r<TA, VS, TC><<<c.Gs, kBlock, 0, s>>>(S, val, rs, v, zp, r, c.flags, cd, n);
+            rk = r;
+            c.launches++;
+        }
+        k_rich_upd_w<TA, VS, TC><<<c.Gs, kBlock, 0, s>>>(S, val, rs, rk, mv, R, k, pos, c.prm.c, gr, c.flags, cd, n);
+        k_rich_upd_z<VS, TC, TP><<<c.G, kBlock, 0, s>>>(rk, mv, zp, zb[k & 1], out, par_misc, R, last ? 1 : 0,
+                                                       c.flags, cd, n);
+        prof_end(c, s);
+        c.launches += 2;
+    }
+}
+
+void launch_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s) {
+    const int a = c.prm.rich_a_prec, v = c.prm.rich_v_prec;
+    if (v == F3R_F16 && a == F3R_F16)
+        rich_go<h16, h16, float, float>(c, c.a16, update, pos, (float *)out, (const float *)par_misc, s);
+    else if (v == F3R_BF16 && a == F3R_BF16)
+        rich_go<b16, b16, float, float>(c, c.abf, update, pos, (float *)out, (const float *)par_misc, s);
+    else if (v == F3R_F32 && a == F3R_F32)
+        rich_go<float, float, float, float>(c, c.a32, update, pos, (float *)out, (const float *)par_misc, s);
+    else if (v == F3R_F64 && a == F3R_F64)
+        rich_go<double, double, double, double>(c, c.ah64, update, pos, (double *)out, (const double *)par_misc, s);
+}
+
+// Stand-alone call: sigma from max|x|, then the cast into the Richardson input.
+void launch_rich_prep(Ctx &c, const void *x, cudaStream_t s) {
+    const bool p64 = c.L[c.prm.nlevels - 1].v_prec == F3R_F64;
+    const int ws = (c.prm.scale_cast && (c.prm.rich_v_prec == F3R_F16 || c.prm.rich_v_prec == F3R_BF16)) ? 1 : 0;
+    if (p64) {
+        GridRed<double> gr{(double *)c.partials, c.ticket, kMaxDots};
+        k_amax_sigma<double><<<c.G, kBlock, 0, s>>>((const double *)x, c.n, (double *)c.apply_misc, ws, gr);
+        k_cast_scaled<double, double><<<c.G, kBlock, 0, s>>>((const double *)x, (double *)c.rin, c.n,
+                                                              (const double *)c.apply_misc);
+    } else {
+        GridRed<float> gr{(float *)c.partials, c.ticket, kMaxDots};
+        k_amax_sigma<float><<<c.G, kBlock, 0, s>>>((const float *)x, c.n, (float *)c.apply_misc, ws, gr);
+        switch (c.prm.rich_v_prec) {
+            case F3R_F16:
+                k_cast_scaled<float, h16><<<c.G, kBlock, 0, s>>>((const float *)x, (h16 *)c.rin, c.n,
+                                                                 (const float *)c.apply_misc);
+                break;
+            case F3R_BF16:
+                k_cast_scaled<float, b16><<<c.G, kBlock, 0, s>>>((const float *)x, (b16 *)c.rin, c.n,
+                                                                 (const float *)c.apply_misc);
+                break;
+            default:
+                k_cast_scaled<float, float><<<c.G, kBlock, 0, s>>>((const float *)x, (float *)c.rin, c.n,
+                                                                   (const float *)c.apply_misc);
+                break;
+        }
+    }
+    c.launches += 2;
+}
+
+}  // namespace f3r

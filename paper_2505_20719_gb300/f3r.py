@@ -1,0 +1,241 @@
+"""ctypes binding of libf3r.so (include/f3r.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA);
+pointers are passed through unchanged and the library tells host from device
+memory.  There is no CPU fallback: if the library is not built or no GPU is
+usable, calls raise F3RError.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libf3r.so")
+
+F64, F32, F16, BF16 = 0, 1, 2, 3
+PC_IDENTITY, PC_JACOBI = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "not converged",
+          5: "breakdown", 6: "non-finite value", 7: "device wait timed out", 8: "unsupported"}
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE = 0, 1, 2, 3, 4, 5, 6
+
+
+class F3RError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("nlevels", C.c_int), ("m", C.c_int * 4), ("a_prec", C.c_int * 4), ("v_prec", C.c_int * 4),
+        ("rich_m", C.c_int), ("rich_a_prec", C.c_int), ("rich_v_prec", C.c_int), ("m_prec", C.c_int),
+        ("precond", C.c_int), ("c", C.c_int), ("omega_fixed", C.c_double), ("diag_scale", C.c_int),
+        ("row_scale", C.c_int), ("scale_cast", C.c_int), ("cgs_passes", C.c_int), ("tol", C.c_double),
+        ("max_outer", C.c_int), ("use_graphs", C.c_int), ("keep_omega", C.c_int), ("reserved", C.c_int * 7),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("outer_iters", C.c_int), ("restarts", C.c_int), ("rel_res_true", C.c_double),
+        ("m_applies", C.c_int64), ("r_calls", C.c_int64), ("r_update_calls", C.c_int64),
+        ("omega", C.c_double * 8), ("hist", C.POINTER(C.c_double)), ("hist_cap", C.c_int),
+        ("hist_len", C.c_int), ("true_hist", C.POINTER(C.c_double)), ("true_cap", C.c_int),
+        ("true_len", C.c_int), ("t_solve_ms", C.c_double), ("kernel_launches", C.c_int64),
+        ("graph_launches", C.c_int64),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """Load libf3r.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise F3RError(ERR_CUDA, f"libf3r.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.f3r_default_params.argtypes = [C.POINTER(Params)]
+        L.f3r_setup.argtypes = [C.POINTER(vp), C.c_int32, C.c_int64, vp, vp, vp, C.POINTER(Params), vp]
+        L.f3r_solve.argtypes = [vp, vp, vp, C.POINTER(Stats), vp]
+        L.f3r_spmv.argtypes = [vp, C.c_int, C.c_int, vp, vp, vp]
+        L.f3r_apply.argtypes = [vp, C.c_int, vp, vp, vp]
+        L.f3r_get_rich_state.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
+        L.f3r_set_rich_state.argtypes = [vp, C.POINTER(C.c_double), C.c_int64]
+        L.f3r_export.argtypes = [vp, C.c_int, vp]
+        L.f3r_device_bytes.argtypes = [vp]
+        L.f3r_device_bytes.restype = C.c_int64
+        L.f3r_destroy.argtypes = [vp]
+        L.f3r_status_str.restype = C.c_char_p
+        for name in ("f3r_default_params", "f3r_setup", "f3r_solve", "f3r_spmv", "f3r_apply",
+                     "f3r_get_rich_state", "f3r_set_rich_state", "f3r_export"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return C.c_void_p(a.ctypes.data)
+    raise TypeError(type(a))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _check(code, where):
+    if code != OK:
+        raise F3RError(code, where)
+
+
+def _set(p, kw):
+    for k, v in kw.items():
+        if k in ("m", "a_prec", "v_prec"):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _check(lib().f3r_default_params(C.byref(p)), "f3r_default_params")
+    return _set(p, kw)
+
+
+def preset(name: str, **kw) -> Params:
+    """Named configurations: fp16-F3R (Table 1), bf16-F3R (bf16 inner storage
+    with per-row scaling), fp32-F3R and fp64-F3R (Sec. 5), fgmres64 (fp64
+    restarted FGMRES(64) with M, Sec. 5)."""
+    if name == "fp16-F3R":
+        p = default_params()
+    elif name == "bf16-F3R":
+        p = default_params(a_prec=[F64, F32, BF16, BF16], rich_a_prec=BF16, rich_v_prec=BF16, m_prec=BF16,
+                           row_scale=1)
+    elif name == "fp32-F3R":
+        p = default_params(a_prec=[F64, F32, F32, F32], rich_a_prec=F32, rich_v_prec=F32, m_prec=F32)
+    elif name == "fp64-F3R":
+        p = default_params(a_prec=[F64, F64, F64, F64], v_prec=[F64, F64, F64, F64], rich_a_prec=F64,
+                           rich_v_prec=F64, m_prec=F64)
+    elif name == "fgmres64":
+        p = default_params(nlevels=1, m=[64, 0, 0, 0], rich_m=0, m_prec=F64, max_outer=19200)
+    else:
+        raise KeyError(name)
+    return _set(p, kw)
+
+
+class Result:
+    def __init__(self, st: Stats, hist, true_hist):
+        self.status = st.status
+        self.outer_iters = st.outer_iters
+        self.restarts = st.restarts
+        self.rel_res_true = st.rel_res_true
+        self.m_applies = st.m_applies
+        self.r_calls = st.r_calls
+        self.r_update_calls = st.r_update_calls
+        self.omega = list(st.omega)
+        self.hist = hist
+        self.true_hist = true_hist
+        self.t_solve_ms = st.t_solve_ms
+        self.kernel_launches = st.kernel_launches
+        self.graph_launches = st.graph_launches
+
+
+class Solver:
+    """One f3r_ctx: the matrix set up on the current CUDA device."""
+
+    def __init__(self, rowptr, colidx, val, params: Params = None, stream=None):
+        self.h = C.c_void_p()
+        n = len(rowptr) - 1
+        nnz = int(rowptr[-1])
+        self.n = n
+        self.params = params if params is not None else default_params()
+        _check(lib().f3r_setup(C.byref(self.h), n, nnz, _ptr(rowptr), _ptr(colidx), _ptr(val),
+                               C.byref(self.params), _stream(stream)), "f3r_setup")
+
+    @classmethod
+    def from_problem(cls, prob, params: Params = None, stream=None):
+        return cls(np.ascontiguousarray(prob.rowptr, dtype=np.int32),
+                   np.ascontiguousarray(prob.colidx, dtype=np.int32),
+                   np.ascontiguousarray(prob.val, dtype=np.float64), params, stream)
+
+    def close(self):
+        if self.h and _lib is not None:
+            _lib.f3r_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b, x, stream=None, hist_cap: int = 4096, check: bool = False) -> Result:
+        """x holds x0 on entry and the solution on exit (host or device arrays)."""
+        hist = np.zeros(hist_cap)
+        th = np.zeros(256)
+        st = Stats()
+        st.hist = hist.ctypes.data_as(C.POINTER(C.c_double))
+        st.hist_cap = hist_cap
+        st.true_hist = th.ctypes.data_as(C.POINTER(C.c_double))
+        st.true_cap = 256
+        code = lib().f3r_solve(self.h, _ptr(b), _ptr(x), C.byref(st), _stream(stream))
+        if code not in (OK, NOT_CONVERGED, ERR_NONFINITE) or (check and code != OK):
+            raise F3RError(code, "f3r_solve")
+        return Result(st, hist[:min(st.hist_len, hist_cap)].copy(), th[:min(st.true_len, 256)].copy())
+
+    def spmv(self, p: int, vp: int, x, y, stream=None):
+        _check(lib().f3r_spmv(self.h, p, vp, _ptr(x), _ptr(y), _stream(stream)), "f3r_spmv")
+
+    def apply(self, level: int, x, z, stream=None):
+        _check(lib().f3r_apply(self.h, level, _ptr(x), _ptr(z), _stream(stream)), "f3r_apply")
+
+    def rich_state(self):
+        om = (C.c_double * 8)()
+        cn = C.c_int64()
+        _check(lib().f3r_get_rich_state(self.h, om, C.byref(cn)), "f3r_get_rich_state")
+        return list(om), cn.value
+
+    def set_rich_state(self, omega, c_ntr: int):
+        om = (C.c_double * 8)(*([float(w) for w in omega] + [1.0] * (8 - len(omega))))
+        _check(lib().f3r_set_rich_state(self.h, om, c_ntr), "f3r_set_rich_state")
+
+    def export(self, which: int, nnz: int = None) -> np.ndarray:
+        """Set-up arrays in CSR order: 0 d, 1 A^ f64, 2 A^ f32, 3 A^/s f16 bits,
+        4 A^/s bf16 bits, 5 row scales, 6 M (m_prec)."""
+        n = self.n
+        if which == 0:
+            out = np.empty(n, np.float64)
+        elif which == 1:
+            out = np.empty(nnz, np.float64)
+        elif which == 2:
+            out = np.empty(nnz, np.float32)
+        elif which in (3, 4):
+            out = np.empty(nnz, np.uint16)
+        elif which == 5:
+            out = np.empty(n, np.float32)
+        else:
+            mp = self.params.m_prec
+            out = np.empty(n, {F64: np.float64, F32: np.float32}.get(mp, np.uint16))
+        _check(lib().f3r_export(self.h, which, _ptr(out)), "f3r_export")
+        return out
+
+    @property
+    def device_bytes(self) -> int:
+        return lib().f3r_device_bytes(self.h)
