@@ -263,19 +263,12 @@ def main():
     value = ms_per_solve / ws
 
     # ---- per-kernel device time inside one solve (events on the launching stream)
-    f3r.lib().f3r_profile_enable(s.h, 1)
+    s.profile(True)
     x.zero_()
     s.solve(b, x, stream=stream)
     torch.cuda.synchronize()
-    prof = {}
-    for slot in range(f3r.lib().f3r_profile_slots()):
-        cnt = f3r.C.c_int64()
-        tms = f3r.C.c_double()
-        f3r.lib().f3r_profile_get(s.h, slot, f3r.C.byref(cnt), f3r.C.byref(tms))
-        if cnt.value:
-            name = f3r.lib().f3r_profile_slot_name(slot).decode() + f"_L{slot % 4}"
-            prof[name] = {"launches": cnt.value, "ms": tms.value}
-    f3r.lib().f3r_profile_enable(s.h, 0)
+    prof = s.profile_report()
+    s.profile(False)
     tot = sum(v["ms"] for v in prof.values())
     for v in prof.values():
         v["share"] = v["ms"] / tot if tot else 0.0

@@ -71,6 +71,13 @@ def lib():
         L.f3r_device_bytes.restype = C.c_int64
         L.f3r_destroy.argtypes = [vp]
         L.f3r_status_str.restype = C.c_char_p
+        L.f3r_profile_enable.argtypes = [vp, C.c_int]
+        L.f3r_profile_enable.restype = C.c_int
+        L.f3r_profile_get.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+        L.f3r_profile_get.restype = C.c_int
+        L.f3r_profile_slots.restype = C.c_int
+        L.f3r_profile_slot_name.argtypes = [C.c_int]
+        L.f3r_profile_slot_name.restype = C.c_char_p
         for name in ("f3r_default_params", "f3r_setup", "f3r_solve", "f3r_spmv", "f3r_apply",
                      "f3r_get_rich_state", "f3r_set_rich_state", "f3r_export"):
             getattr(L, name).restype = C.c_int
@@ -234,6 +241,21 @@ class Solver:
             mp = self.params.m_prec
             out = np.empty(n, {F64: np.float64, F32: np.float32}.get(mp, np.uint16))
         _check(lib().f3r_export(self.h, which, _ptr(out)), "f3r_export")
+        return out
+
+    def profile(self, enable: bool):
+        """Turn the per-kernel event profiler on (resetting it) or off."""
+        _check(lib().f3r_profile_enable(self.h, 1 if enable else 0), "f3r_profile_enable")
+
+    def profile_report(self) -> dict:
+        """{'<kind>_L<level>': {'launches': n, 'ms': total device ms}} of the profiled launches."""
+        out = {}
+        for slot in range(lib().f3r_profile_slots()):
+            cnt, tms = C.c_int64(), C.c_double()
+            _check(lib().f3r_profile_get(self.h, slot, C.byref(cnt), C.byref(tms)), "f3r_profile_get")
+            if cnt.value:
+                name = lib().f3r_profile_slot_name(slot).decode() + f"_L{slot % 4}"
+                out[name] = {"launches": cnt.value, "ms": tms.value}
         return out
 
     @property
