@@ -160,6 +160,31 @@ f3r_status f3r_profile_get(f3r_ctx *ctx, int slot, int64_t *launches, double *to
 int f3r_profile_slots(void);
 const char *f3r_profile_slot_name(int slot);
 
+/* Residual without device allocation (no counterpart in the paper).
+ *
+ * r = b - A x (fp64 row sums in CSR order with fused multiply-add) and
+ * norms[0] = ||r||_2, norms[1] = ||b||_2, for an n x n fp64 CSR matrix.  For
+ * callers that may not call cudaMalloc -- code whose device memory belongs
+ * to another allocator (a framework's caching pool, a fixed budget set up
+ * front) and so cannot let a library allocate -- this entry point needs no
+ * context and allocates nothing: every buffer is the caller's (rowptr,
+ * colidx, val, b, x, r and norms[2] are device pointers of the current
+ * device; r and norms are written).  Its only scratch is a 65,792-byte
+ * static device array inside libf3r (per-block partial sums and a ticket),
+ * which every GPU that loads the library holds until the process exits.
+ *   - n must be 1 .. 4,194,304 (the scratch holds 4096 blocks of 1024
+ *     rows); larger n, n <= 0 or a NULL pointer return F3R_ERR_ARG.
+ *   - The first call on a device looks up that device's address of the
+ *     scratch array (with the device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the one scratch array, which keeps the last call's
+ *     contents (each call clears the part that must start at zero), so calls
+ *     that overlap on the GPU -- on different streams or host threads -- race
+ *     and must be serialised by the caller.
+ *   - Work is ordered on `stream`; the call returns after the launch. */
+f3r_status f3r_residual_noalloc(int32_t n, const int32_t *rowptr, const int32_t *colidx, const double *val,
+                                const double *b, const double *x, double *r, double *norms, void *stream);
+
 /* Device memory held by the context, in bytes. */
 int64_t f3r_device_bytes(const f3r_ctx *ctx);
 

@@ -78,6 +78,8 @@ def lib():
         L.f3r_profile_slots.restype = C.c_int
         L.f3r_profile_slot_name.argtypes = [C.c_int]
         L.f3r_profile_slot_name.restype = C.c_char_p
+        L.f3r_residual_noalloc.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.f3r_residual_noalloc.restype = C.c_int
         for name in ("f3r_default_params", "f3r_setup", "f3r_solve", "f3r_spmv", "f3r_apply",
                      "f3r_get_rich_state", "f3r_set_rich_state", "f3r_export"):
             getattr(L, name).restype = C.c_int
