@@ -203,3 +203,19 @@ __device__ __forceinline__ TC sell_row(const Sell &S, const TA *__restrict__ val
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace f3r
+
+namespace f3r {
+// 16-byte packs for vectorised streaming of Krylov vectors (float4 / double2)
+template <class T, int N> struct alignas(sizeof(T) * N) Pack {
+    T v[N];
+};
+template <class T> struct PackN {
+    static constexpr int N = 16 / sizeof(T);
+};
+template <class T, int N> __device__ __forceinline__ Pack<T, N> ldp(const T *p) {
+    return *reinterpret_cast<const Pack<T, N> *>(p);
+}
+template <class T, int N> __device__ __forceinline__ void stp(T *p, const Pack<T, N> &x) {
+    *reinterpret_cast<Pack<T, N> *>(p) = x;
+}
+}  // namespace f3r

@@ -20,6 +20,7 @@ struct Readback {
     double est;       // |g_{j+1}| / ||b||
     double rel;       // true relative residual at a cycle start
     double nb;        // ||b||
+    int err;          // device error word
     int flags[16];    // copy of all levels' flags
     unsigned long long counters[4];
 };
@@ -51,6 +52,7 @@ struct Ctx {
     int ld = 0;            // stride between vectors of a basis
     // sliced ELLPACK (slices of 32 rows, column-major inside a slice)
     int nslices = 0;
+    int wmax = 0;              // widest slice (entries per row)
     long long nsell = 0;
     int *sptr = nullptr, *col = nullptr, *rowptr = nullptr;
     double *a64 = nullptr;      // original A
@@ -75,6 +77,8 @@ struct Ctx {
     unsigned *ticket = nullptr;
     int G = 1, Gs = 1, G1 = 1;
     int *flags = nullptr;       // 4 ints per level
+    int *err = nullptr;         // device error word (bounded waits that gave up)
+    bool staged = true;         // stage SELL slices through shared memory
     int *jdev = nullptr;
     void *zst = nullptr;        // the outer level's preconditioner output (fp64)
     void *apply_misc = nullptr; // scalars of a stand-alone Richardson call
@@ -150,5 +154,13 @@ void launch_rich_prep(Ctx &c, const void *x, cudaStream_t s);
 
 // sizes
 int prec_bytes(int p);
+
+// Shared-memory staging plan of one SELL kernel: ring depth S, bytes per
+// stage, dynamic shared memory per block and the grid (resident blocks).
+struct StagePlan {
+    int S = 0, stage_bytes = 0, smem = 0;
+};
+StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize);
+int maxd_bucket(int m);
 
 }  // namespace f3r

@@ -11,6 +11,8 @@
 //   k_normalize   : V[j+1] = w / ||w|| and the child's input (cast, scaling)
 // and finally k_combine: z = sum_k y_k Z[k] into the parent's slot.
 #pragma once
+#include <utility>
+
 #include "common.cuh"
 
 namespace f3r {
@@ -141,31 +143,57 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dots(Sell S, const TA *__restri
     });
 }
 
-// w -= V[0..j] h (fma in l order), then hB = V[0..j]^T w
-template <class T>
+// w -= V[0..j] h (fma in l order), then hB = V[0..j]^T w.  Streams 16-byte
+// packs; MAXD bounds j + 1 so the register footprint follows the level size.
+template <class T, int MAXD>
 __global__ void __launch_bounds__(kBlock) k_cgs_pass(LevelDev<T> L, int j, GridRed<T> gr) {
     if (stopped(L.flags, L.depth)) return;
-    __shared__ T hs[kMaxDots];
+    constexpr int N = PackN<T>::N;
+    __shared__ T hs[MAXD];
     if (threadIdx.x <= j) hs[threadIdx.x] = L.hA()[threadIdx.x];
     __syncthreads();
-    T acc[kMaxDots];
+    T acc[MAXD];
 #pragma unroll
-    for (int l = 0; l < kMaxDots; ++l) acc[l] = (T)0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
-        T v[kMaxDots];
-        T wi = L.w[i];
+    for (int l = 0; l < MAXD; ++l) acc[l] = (T)0;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int nq = L.n / N;
+    T *__restrict__ w = L.w;
+    const T *__restrict__ V = L.V;
+    for (int q = tid; q < nq; q += nth) {
+        Pack<T, N> wv = ldp<T, N>(w + (size_t)q * N);
+        Pack<T, N> v[MAXD];
 #pragma unroll
-        for (int l = 0; l < kMaxDots; ++l)
+        for (int l = 0; l < MAXD; ++l)
+            if (l <= j) v[l] = ldp<T, N>(V + (size_t)l * L.ld + (size_t)q * N);
+#pragma unroll
+        for (int l = 0; l < MAXD; ++l)
             if (l <= j) {
-                v[l] = L.V[(size_t)l * L.ld + i];
+#pragma unroll
+                for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-hs[l], v[l].v[e], wv.v[e]);
+            }
+        stp<T, N>(w + (size_t)q * N, wv);
+#pragma unroll
+        for (int l = 0; l < MAXD; ++l)
+            if (l <= j) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) acc[l] = fma_rn(v[l].v[e], wv.v[e], acc[l]);
+            }
+    }
+    for (int i = nq * N + tid; i < L.n; i += nth) {
+        T wi = w[i];
+        T v[MAXD];
+#pragma unroll
+        for (int l = 0; l < MAXD; ++l)
+            if (l <= j) {
+                v[l] = V[(size_t)l * L.ld + i];
                 wi = fma_rn(-hs[l], v[l], wi);
             }
-        L.w[i] = wi;
+        w[i] = wi;
 #pragma unroll
-        for (int l = 0; l < kMaxDots; ++l)
+        for (int l = 0; l < MAXD; ++l)
             if (l <= j) acc[l] = fma_rn(v[l], wi, acc[l]);
     }
-    grid_reduce<T, kMaxDots>(acc, j + 1, false, gr, [&](T *res) {
+    grid_reduce<T, MAXD>(acc, j + 1, false, gr, [&](T *res) {
         T *hB = L.hB();
         for (int l = 0; l <= j; ++l) hB[l] = res[l];
     });
@@ -173,26 +201,50 @@ __global__ void __launch_bounds__(kBlock) k_cgs_pass(LevelDev<T> L, int j, GridR
 
 // w -= V[0..j] h_last; ||w||^2 and max|w|; Givens step with column hA (+ hB);
 // the scale of the child's 16-bit cast of V[j+1] from max|w| / ||w||.
-template <class T>
+template <class T, int MAXD>
 __global__ void __launch_bounds__(kBlock) k_cgs_final(LevelDev<T> L, int j, int passes, int last_iter,
                                                       int want_sigma, GridRed<T> gr) {
     if (stopped(L.flags, L.depth)) return;
-    __shared__ T hs[kMaxDots];
+    constexpr int N = PackN<T>::N;
+    __shared__ T hs[MAXD];
     const T *hl = (passes == 2) ? L.hB() : L.hA();
     if (threadIdx.x <= j) hs[threadIdx.x] = hl[threadIdx.x];
     __syncthreads();
     T acc[2] = {(T)0, (T)0};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
-        T wi = L.w[i];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int nq = L.n / N;
+    T *__restrict__ w = L.w;
+    const T *__restrict__ V = L.V;
+    for (int q = tid; q < nq; q += nth) {
+        Pack<T, N> wv = ldp<T, N>(w + (size_t)q * N);
+        Pack<T, N> v[MAXD];
 #pragma unroll
-        for (int l = 0; l < kMaxDots; ++l)
-            if (l <= j) wi = fma_rn(-hs[l], L.V[(size_t)l * L.ld + i], wi);
-        L.w[i] = wi;
+        for (int l = 0; l < MAXD; ++l)
+            if (l <= j) v[l] = ldp<T, N>(V + (size_t)l * L.ld + (size_t)q * N);
+#pragma unroll
+        for (int l = 0; l < MAXD; ++l)
+            if (l <= j) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-hs[l], v[l].v[e], wv.v[e]);
+            }
+        stp<T, N>(w + (size_t)q * N, wv);
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+            acc[0] = fma_rn(wv.v[e], wv.v[e], acc[0]);
+            acc[1] = fmax(acc[1], fabs(wv.v[e]));
+        }
+    }
+    for (int i = nq * N + tid; i < L.n; i += nth) {
+        T wi = w[i];
+#pragma unroll
+        for (int l = 0; l < MAXD; ++l)
+            if (l <= j) wi = fma_rn(-hs[l], V[(size_t)l * L.ld + i], wi);
+        w[i] = wi;
         acc[0] = fma_rn(wi, wi, acc[0]);
         acc[1] = fmax(acc[1], fabs(wi));
     }
     grid_reduce<T, 2>(acc, 1, true, gr, [&](T *res) {
-        T hcol[kMaxDots];
+        T hcol[MAXD];
         const T *hA = L.hA(), *hB = L.hB();
         for (int l = 0; l <= j; ++l) hcol[l] = (passes == 2) ? add_rn(hA[l], hB[l]) : hA[l];
         T hn = sqrt_rn(res[0]);
@@ -230,19 +282,39 @@ template <class T, class TC, int CHILD>
 __global__ void __launch_bounds__(kBlock) k_normalize(LevelDev<T> L, const T *src, int dst, int check_depth,
                                                       ChildOut<TC> co, GridRed<T> gr) {
     if (stopped(L.flags, check_depth)) return;
+    constexpr int N = PackN<T>::N;
     const int jd = L.jptr ? (*L.jptr + dst) : dst;
     T *out = L.V + (size_t)jd * L.ld;
     const T inv = L.misc()[MS_INV];
     const T sig = L.misc()[MS_SIGMA];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int nq = L.n / N;
     if constexpr (CHILD == CHILD_F) {
         TC acc[2] = {(TC)0, (TC)0};
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
-            const T v = mul_rn(src[i], inv);
-            out[i] = v;
+        auto one = [&](int i, T sv) {
+            const T v = mul_rn(sv, inv);
             const TC c = co.dsc ? Store<TC>::from(mul_rn(co.dsc[i], (double)v)) : Store<TC>::from(v);
-            co.x[i] = c;
             acc[0] = fma_rn(c, c, acc[0]);
             acc[1] = fmax(acc[1], fabs(c));
+            return std::pair<T, TC>(v, c);
+        };
+        for (int q = tid; q < nq; q += nth) {
+            const Pack<T, N> sp = ldp<T, N>(src + (size_t)q * N);
+            Pack<T, N> op;
+            Pack<TC, N> cp;
+#pragma unroll
+            for (int e = 0; e < N; ++e) {
+                auto vc = one(q * N + e, sp.v[e]);
+                op.v[e] = vc.first;
+                cp.v[e] = vc.second;
+            }
+            stp<T, N>(out + (size_t)q * N, op);
+            stp<TC, N>(co.x + (size_t)q * N, cp);
+        }
+        for (int i = nq * N + tid; i < L.n; i += nth) {
+            auto vc = one(i, src[i]);
+            out[i] = vc.first;
+            co.x[i] = vc.second;
         }
         GridRed<TC> grc{(TC *)gr.partials, gr.ticket, gr.stride};
         grid_reduce<TC, 2>(acc, 1, true, grc, [&](TC *res) {
@@ -269,7 +341,20 @@ __global__ void __launch_bounds__(kBlock) k_normalize(LevelDev<T> L, const T *sr
             if (L.jptr && dst == 1) atomicAdd(const_cast<int *>(L.jptr), 1);  // closes outer iteration j
         });
     } else {
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
+        for (int q = tid; q < nq; q += nth) {
+            const Pack<T, N> sp = ldp<T, N>(src + (size_t)q * N);
+            Pack<T, N> op;
+#pragma unroll
+            for (int e = 0; e < N; ++e) op.v[e] = mul_rn(sp.v[e], inv);
+            stp<T, N>(out + (size_t)q * N, op);
+            if constexpr (CHILD == CHILD_R) {
+                Pack<TC, N> cp;
+#pragma unroll
+                for (int e = 0; e < N; ++e) cp.v[e] = Store<TC>::from(mul_rn(sig, op.v[e]));
+                stp<TC, N>(co.x + (size_t)q * N, cp);
+            }
+        }
+        for (int i = nq * N + tid; i < L.n; i += nth) {
             const T v = mul_rn(src[i], inv);
             out[i] = v;
             if constexpr (CHILD == CHILD_R) co.x[i] = Store<TC>::from(mul_rn(sig, v));

@@ -2,6 +2,7 @@
 // each level (Table 1).
 #include "ctx.h"
 #include "kernels.cuh"
+#include "staged.cuh"
 
 namespace f3r {
 
@@ -129,52 +130,84 @@ void launch_normalize(Ctx &c, int d, bool from_w, int dst, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ SpMV + dots
+// grid of a staged kernel: the blocks that fit on the SMs at once (<= 4 per SM)
+template <class K> static int staged_grid(Ctx &c, K kern, int smem, int work_blocks) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, smem);
+    nb = std::max(1, std::min(nb, 4));
+    return std::max(1, std::min(c.nsm * nb, work_blocks));
+}
+
+template <class TA, class T, int S, int MAXD>
+static void spmv_dots_st_go(Ctx &c, int d, int j, const TA *val, const float *rs, const StagePlan &pl,
+                            cudaStream_t s) {
+    auto kern = k_spmv_dots_st<TA, T, S, MAXD>;
+    const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
+    kern<<<g, kBlock, pl.smem, s>>>(sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots),
+                                    StageCfg{pl.stage_bytes, c.err});
+}
+
+template <class TA, class T>
+static void spmv_dots_go(Ctx &c, int d, int j, const TA *val, const float *rs, cudaStream_t s) {
+    const StagePlan pl = plan_stage(c, sizeof(TA), c.L[d].m, sizeof(T));
+    const int md = maxd_bucket(c.L[d].m);
+    if (pl.S == 3) {
+        if (md == 4) spmv_dots_st_go<TA, T, 3, 4>(c, d, j, val, rs, pl, s);
+        else if (md == 8) spmv_dots_st_go<TA, T, 3, 8>(c, d, j, val, rs, pl, s);
+        else spmv_dots_st_go<TA, T, 3, 16>(c, d, j, val, rs, pl, s);
+    } else if (pl.S == 2) {
+        if (md == 4) spmv_dots_st_go<TA, T, 2, 4>(c, d, j, val, rs, pl, s);
+        else if (md == 8) spmv_dots_st_go<TA, T, 2, 8>(c, d, j, val, rs, pl, s);
+        else spmv_dots_st_go<TA, T, 2, 16>(c, d, j, val, rs, pl, s);
+    } else {
+        k_spmv_dots<TA, T><<<c.Gs, kBlock, 0, s>>>(sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots));
+    }
+}
+
 void launch_spmv_dots(Ctx &c, int d, int j, cudaStream_t s) {
-    const Sell S = sell_of(c);
     const float *rs = c.prm.row_scale ? c.rs : nullptr;
     prof_begin(c, PK_SPMV_DOTS, d, s);
     if (c.L[d].v_prec == F3R_F64) {
-        k_spmv_dots<double, double><<<c.Gs, kBlock, 0, s>>>(S, c.ah64, nullptr, levdev<double>(c, d), j,
-                                                             gred<double>(c, kMaxDots));
+        spmv_dots_go<double, double>(c, d, j, c.ah64, nullptr, s);
     } else {
         switch (c.L[d].a_prec) {
-            case F3R_F32:
-                k_spmv_dots<float, float><<<c.Gs, kBlock, 0, s>>>(S, c.a32, nullptr, levdev<float>(c, d), j,
-                                                                  gred<float>(c, kMaxDots));
-                break;
-            case F3R_F16:
-                k_spmv_dots<h16, float><<<c.Gs, kBlock, 0, s>>>(S, c.a16, rs, levdev<float>(c, d), j,
-                                                                gred<float>(c, kMaxDots));
-                break;
-            default:
-                k_spmv_dots<b16, float><<<c.Gs, kBlock, 0, s>>>(S, c.abf, rs, levdev<float>(c, d), j,
-                                                                gred<float>(c, kMaxDots));
-                break;
+            case F3R_F32: spmv_dots_go<float, float>(c, d, j, c.a32, nullptr, s); break;
+            case F3R_F16: spmv_dots_go<h16, float>(c, d, j, c.a16, rs, s); break;
+            default: spmv_dots_go<b16, float>(c, d, j, c.abf, rs, s); break;
         }
     }
     prof_end(c, s);
     c.launches++;
 }
 
+template <class T, int MAXD> static void cgs_go(Ctx &c, int d, int j, bool final_pass, bool last, cudaStream_t s) {
+    if (final_pass)
+        k_cgs_final<T, MAXD><<<c.G, kBlock, 0, s>>>(levdev<T>(c, d), j, c.prm.cgs_passes, last ? 1 : 0,
+                                                    want_sigma(c, d), gred<T>(c, kMaxDots));
+    else
+        k_cgs_pass<T, MAXD><<<c.G, kBlock, 0, s>>>(levdev<T>(c, d), j, gred<T>(c, kMaxDots));
+}
+
+template <class T> static void cgs_dispatch(Ctx &c, int d, int j, bool final_pass, bool last, cudaStream_t s) {
+    const int md = maxd_bucket(c.L[d].m);
+    if (md == 4) cgs_go<T, 4>(c, d, j, final_pass, last, s);
+    else if (md == 8) cgs_go<T, 8>(c, d, j, final_pass, last, s);
+    else cgs_go<T, 16>(c, d, j, final_pass, last, s);
+}
+
 void launch_cgs_pass(Ctx &c, int d, int j, cudaStream_t s) {
     prof_begin(c, PK_CGS_PASS, d, s);
-    if (c.L[d].v_prec == F3R_F64)
-        k_cgs_pass<double><<<c.G, kBlock, 0, s>>>(levdev<double>(c, d), j, gred<double>(c, kMaxDots));
-    else
-        k_cgs_pass<float><<<c.G, kBlock, 0, s>>>(levdev<float>(c, d), j, gred<float>(c, kMaxDots));
+    if (c.L[d].v_prec == F3R_F64) cgs_dispatch<double>(c, d, j, false, false, s);
+    else cgs_dispatch<float>(c, d, j, false, false, s);
     prof_end(c, s);
     c.launches++;
 }
 
 void launch_cgs_final(Ctx &c, int d, int j, bool last, cudaStream_t s) {
-    const int ws = want_sigma(c, d);
     prof_begin(c, PK_CGS_FINAL, d, s);
-    if (c.L[d].v_prec == F3R_F64)
-        k_cgs_final<double><<<c.G, kBlock, 0, s>>>(levdev<double>(c, d), j, c.prm.cgs_passes, last ? 1 : 0, ws,
-                                                    gred<double>(c, kMaxDots));
-    else
-        k_cgs_final<float><<<c.G, kBlock, 0, s>>>(levdev<float>(c, d), j, c.prm.cgs_passes, last ? 1 : 0, ws,
-                                                   gred<float>(c, kMaxDots));
+    if (c.L[d].v_prec == F3R_F64) cgs_dispatch<double>(c, d, j, true, last, s);
+    else cgs_dispatch<float>(c, d, j, true, last, s);
     prof_end(c, s);
     c.launches++;
 }
@@ -243,8 +276,21 @@ __global__ void __launch_bounds__(kBlock) k_outer_store_z(LevelDev<double> L, co
 void launch_outer_step(Ctx &c, cudaStream_t s) {
     LevelDev<double> L = levdev<double>(c, 0);
     prof_begin(c, PK_OUTER_SPMV, 0, s);
-    k_outer_store_z<<<c.G, kBlock, 0, s>>>(L, (const double *)c.zst);
-    k_outer_spmv<<<c.Gs, kBlock, 0, s>>>(sell_of(c), c.a64, L);
+    const StagePlan pl = plan_stage(c, sizeof(double), 0, 8);
+    if (pl.S == 3) {
+        auto kern = k_outer_spmv_st<3>;
+        const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
+        kern<<<g, kBlock, pl.smem, s>>>(sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err});
+        c.launches--;
+    } else if (pl.S == 2) {
+        auto kern = k_outer_spmv_st<2>;
+        const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
+        kern<<<g, kBlock, pl.smem, s>>>(sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err});
+        c.launches--;
+    } else {
+        k_outer_store_z<<<c.G, kBlock, 0, s>>>(L, (const double *)c.zst);
+        k_outer_spmv<<<c.Gs, kBlock, 0, s>>>(sell_of(c), c.a64, L);
+    }
     prof_end(c, s);
     double *part = (double *)c.partials;
     prof_begin(c, PK_OUTER_CGS, 0, s);
@@ -294,45 +340,54 @@ __global__ void __launch_bounds__(kBlock) k_spmv(Sell S, const TA *__restrict__ 
     }
 }
 
+template <class TA, class TX, class TY>
+static void spmv_go(Ctx &c, const TA *val, const float *rs, const TX *x, TY *y, cudaStream_t s) {
+    const StagePlan pl = plan_stage(c, sizeof(TA), 0, 4);
+    const StageCfg cfg{pl.stage_bytes, c.err};
+    if (pl.S == 3) {
+        auto kern = k_spmv_st<TA, TX, TY, 3>;
+        kern<<<staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices)), kBlock, pl.smem, s>>>(sell_of(c), val, rs,
+                                                                                                x, y, cfg);
+    } else if (pl.S == 2) {
+        auto kern = k_spmv_st<TA, TX, TY, 2>;
+        kern<<<staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices)), kBlock, pl.smem, s>>>(sell_of(c), val, rs,
+                                                                                                x, y, cfg);
+    } else {
+        k_spmv<TA, TX, TY><<<c.Gs, kBlock, 0, s>>>(sell_of(c), val, rs, x, y);
+    }
+}
+
 f3r_status launch_spmv(Ctx &c, int p, int vp, const void *x, void *y, cudaStream_t s) {
-    const Sell S = sell_of(c);
     const float *rs = c.prm.row_scale ? c.rs : nullptr;
-    const int g = c.Gs;
+    f3r_status st = F3R_OK;
     prof_begin(c, PK_SPMV, p, s);
     switch (p) {
         case F3R_F64:
-            if (vp != F3R_F64) return F3R_ERR_ARG;
-            k_spmv<double, double, double><<<g, kBlock, 0, s>>>(S, c.a64, nullptr, (const double *)x, (double *)y);
+            if (vp != F3R_F64) st = F3R_ERR_ARG;
+            else spmv_go<double, double, double>(c, c.a64, nullptr, (const double *)x, (double *)y, s);
             break;
         case F3R_F32:
-            if (!c.a32 || vp != F3R_F32) return F3R_ERR_ARG;
-            k_spmv<float, float, float><<<g, kBlock, 0, s>>>(S, c.a32, nullptr, (const float *)x, (float *)y);
+            if (!c.a32 || vp != F3R_F32) st = F3R_ERR_ARG;
+            else spmv_go<float, float, float>(c, c.a32, nullptr, (const float *)x, (float *)y, s);
             break;
         case F3R_F16:
-            if (!c.a16) return F3R_ERR_ARG;
-            if (vp == F3R_F32)
-                k_spmv<h16, float, float><<<g, kBlock, 0, s>>>(S, c.a16, rs, (const float *)x, (float *)y);
-            else if (vp == F3R_F16)
-                k_spmv<h16, h16, float><<<g, kBlock, 0, s>>>(S, c.a16, rs, (const h16 *)x, (float *)y);
-            else
-                return F3R_ERR_ARG;
+            if (!c.a16) st = F3R_ERR_ARG;
+            else if (vp == F3R_F32) spmv_go<h16, float, float>(c, c.a16, rs, (const float *)x, (float *)y, s);
+            else if (vp == F3R_F16) spmv_go<h16, h16, float>(c, c.a16, rs, (const h16 *)x, (float *)y, s);
+            else st = F3R_ERR_ARG;
             break;
         case F3R_BF16:
-            if (!c.abf) return F3R_ERR_ARG;
-            if (vp == F3R_F32)
-                k_spmv<b16, float, float><<<g, kBlock, 0, s>>>(S, c.abf, rs, (const float *)x, (float *)y);
-            else if (vp == F3R_BF16)
-                k_spmv<b16, b16, float><<<g, kBlock, 0, s>>>(S, c.abf, rs, (const b16 *)x, (float *)y);
-            else
-                return F3R_ERR_ARG;
+            if (!c.abf) st = F3R_ERR_ARG;
+            else if (vp == F3R_F32) spmv_go<b16, float, float>(c, c.abf, rs, (const float *)x, (float *)y, s);
+            else if (vp == F3R_BF16) spmv_go<b16, b16, float>(c, c.abf, rs, (const b16 *)x, (float *)y, s);
+            else st = F3R_ERR_ARG;
             break;
         default:
-            prof_end(c, s);
-            return F3R_ERR_ARG;
+            st = F3R_ERR_ARG;
     }
     prof_end(c, s);
-    c.launches++;
-    return F3R_OK;
+    if (st == F3R_OK) c.launches++;
+    return st;
 }
 
 }  // namespace f3r

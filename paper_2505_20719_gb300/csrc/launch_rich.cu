@@ -1,12 +1,23 @@
 // Launchers of the Richardson level (Algorithm 1), dispatching on the
 // storage of A and of the Richardson vectors.
+#include <algorithm>
+
 #include "ctx.h"
 #include "rich.cuh"
+#include "staged.cuh"
 
 namespace f3r {
 
 template <class TC> static RichDev<TC> richdev(Ctx &c) {
     return RichDev<TC>{(TC *)c.omega, (TC *)c.wcur, c.counters, c.c_ntr_base};
+}
+
+template <class K> static int rich_grid(Ctx &c, K kern, int smem) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, smem);
+    nb = std::max(1, std::min(nb, 4));
+    return std::max(1, std::min(c.nsm * nb, ceil_div(c.nslices, kTileSlices)));
 }
 
 template <class TA, class VS, class TC, class TP>
@@ -22,7 +33,19 @@ static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const 
     if (!update) {
         if (m4 == 2) {
             prof_begin(c, PK_RICH2, 0, s);
-            k_rich2<TA, VS, TC, TP><<<c.Gs, kBlock, 0, s>>>(S, val, rs, v, mv, out, par_misc, R, c.flags, cd, n);
+            const StagePlan pl = plan_stage(c, sizeof(TA), 0, 4);
+            const StageCfg cfg{pl.stage_bytes, c.err};
+            if (pl.S == 3) {
+                auto kern = k_rich2_st<TA, VS, TC, TP, 3>;
+                kern<<<rich_grid(c, kern, pl.smem), kBlock, pl.smem, s>>>(S, val, rs, v, mv, out, par_misc, R, c.flags,
+                                                                          cd, n, cfg);
+            } else if (pl.S == 2) {
+                auto kern = k_rich2_st<TA, VS, TC, TP, 2>;
+                kern<<<rich_grid(c, kern, pl.smem), kBlock, pl.smem, s>>>(S, val, rs, v, mv, out, par_misc, R, c.flags,
+                                                                          cd, n, cfg);
+            } else {
+                k_rich2<TA, VS, TC, TP><<<c.Gs, kBlock, 0, s>>>(S, val, rs, v, mv, out, par_misc, R, c.flags, cd, n);
+            }
             prof_end(c, s);
             c.launches++;
         } else {

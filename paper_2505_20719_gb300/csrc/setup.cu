@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "ctx.h"
+#include "stage.cuh"
 
 namespace f3r {
 
@@ -166,6 +167,8 @@ f3r_status build_matrix(Ctx &c, const int *rp, const int *ci, const double *val,
     }
     hp[c.nslices] = (int)tot;
     c.nsell = tot;
+    c.wmax = 0;
+    for (int k = 0; k < c.nslices; ++k) c.wmax = std::max(c.wmax, hw[k]);
     c.sptr = (int *)dalloc(c, sizeof(int) * (c.nslices + 1));
     c.col = (int *)dalloc(c, sizeof(int) * tot);
     if (!c.sptr || !c.col) return F3R_ERR_NOMEM;
@@ -247,6 +250,27 @@ f3r_status export_array(Ctx &c, int which, void *out, cudaStream_t s) {
     cudaFree(tmp);
     return e == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
 }
+
+StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize) {
+    StagePlan p;
+    if (!c.staged) return p;
+    const int sb = stage_bytes_for(c.wmax, asize, n_extra, esize);
+    // 3 stages if four blocks fit an SM, else 2 stages with two blocks, else
+    // 2 stages with one block; wider tiles run unstaged.
+    const int cand[3][2] = {{3, 56 * 1024}, {2, 110 * 1024}, {2, 220 * 1024}};
+    for (auto &cs : cand) {
+        const int smem = 256 + cs[0] * sb;
+        if (smem <= cs[1]) {
+            p.S = cs[0];
+            p.stage_bytes = sb;
+            p.smem = smem;
+            return p;
+        }
+    }
+    return p;
+}
+
+int maxd_bucket(int m) { return m <= 4 ? 4 : (m <= 8 ? 8 : 16); }
 
 int prec_bytes(int p) {
     switch (p) {

@@ -161,8 +161,9 @@ void run_level(Ctx &c, int d, const OutSlot &out, long long &pos, cudaStream_t s
 }
 
 __global__ void k_pack_readback(const double *misc0, const int *flags, const unsigned long long *counters,
-                                Readback *rb) {
+                                const int *err, Readback *rb) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
+        rb->err = *err;
         rb->est = misc0[MS_EST];
         rb->rel = misc0[MS_REL];
         rb->nb = misc0[MS_NB];
@@ -173,7 +174,7 @@ __global__ void k_pack_readback(const double *misc0, const int *flags, const uns
 
 void pack_readback(f3r_ctx *h, cudaStream_t s) {
     Ctx &c = h->c;
-    k_pack_readback<<<1, 32, 0, s>>>((const double *)misc_of(c, 0), c.flags, c.counters, h->rb_dev);
+    k_pack_readback<<<1, 32, 0, s>>>((const double *)misc_of(c, 0), c.flags, c.counters, c.err, h->rb_dev);
     c.launches++;
     cudaMemcpyAsync(c.rb, h->rb_dev, sizeof(Readback), cudaMemcpyDeviceToHost, s);
 }
@@ -329,7 +330,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     c.prm = prm;
     c.n = n;
     c.nnz = nnz;
-    c.ld = (int)(((long long)n + 63) / 64 * 64);
+    c.ld = (int)(((long long)n + 255) / 256 * 256);  // whole 256-row tiles
     if (cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) != cudaSuccess) {
         delete h;
         return F3R_ERR_CUDA;
@@ -405,11 +406,12 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
                                    (size_t)(kMaxOuterM + 2) * c.G1 * sizeof(double));
     c.partials = dalloc(c, pbytes);
     c.ticket = (unsigned *)dalloc(c, sizeof(unsigned) * 4);
+    c.err = (int *)dalloc(c, sizeof(int) * 4);
     c.flags = (int *)dalloc(c, sizeof(int) * 16);
     c.jdev = (int *)dalloc(c, sizeof(int) * 4);
     h->rb_dev = (Readback *)dalloc(c, sizeof(Readback));
     if (!c.omega || !c.wcur || !c.counters || !c.c_ntr_base || !c.zst || !c.apply_misc || !c.partials ||
-        !c.ticket || !c.flags || !c.jdev || !h->rb_dev)
+        !c.ticket || !c.err || !c.flags || !c.jdev || !h->rb_dev)
         return fail(F3R_ERR_NOMEM);
     if (cudaHostAlloc((void **)&c.rb, sizeof(Readback), cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void **)&c.hostval, sizeof(double) * 8, cudaHostAllocDefault) != cudaSuccess)
@@ -460,6 +462,7 @@ f3r_status f3r_solve(f3r_ctx *h, const double *b, double *x, f3r_stats *stats, v
     upload_cntr(c, s);
     cudaMemsetAsync(c.counters, 0, sizeof(unsigned long long) * 4, s);
     cudaMemsetAsync(c.flags, 0, sizeof(int) * 16, s);
+    cudaMemsetAsync(c.err, 0, sizeof(int) * 4, s);
     const long long launches0 = c.launches, glaunch0 = c.graph_launches;
 
     int hist_len = 0, true_len = 0;
@@ -507,6 +510,7 @@ f3r_status f3r_solve(f3r_ctx *h, const double *b, double *x, f3r_stats *stats, v
             ++total;
             c.c_ntr += c.calls_per_outer;
             const Readback &rb = *c.rb;
+            if (rb.err) return F3R_ERR_TIMEOUT;
             const int *fl0 = rb.flags;  // outer level flags
             if (fl0[IF_NONFINITE]) {
                 nonfinite = true;

@@ -1,23 +1,24 @@
 // Shared-memory staging of sliced-ELLPACK slices with bulk asynchronous
 // copies (TMA, cp.async.bulk) and mbarrier completion.
 //
-// Each warp walks its slices s = first, first + stride, ... through a ring of
-// S shared-memory stages.  Lane 0 issues, per slice, one bulk copy for the
-// slice's column indices, one for its values and one per extra row-aligned
-// vector segment (e.g. the Krylov basis rows the fused dot products read),
-// all completing on the stage's mbarrier.  S slices are in flight per warp,
-// which keeps enough bytes moving to cover HBM latency while the lanes
-// gather x from L1/L2 and accumulate.
+// A block walks a contiguous range of tiles (8 consecutive slices = 256
+// rows) through a ring of S shared-memory stages.  One thread issues, per
+// tile, one bulk copy for the tile's column indices, one for its values and
+// one per extra row-aligned vector segment (e.g. the Krylov basis rows the
+// fused dot products read), all completing on the stage's mbarrier.  S tiles
+// are in flight per block, which keeps enough bytes moving to cover HBM
+// latency while the warps gather x (largely from L1, since a block's tiles
+// are neighbours) and accumulate.
 //
-// Every wait is bounded: after kSpinLimit failed polls the kernel records
-// an error code, waits (bounded again) for its own copies still in flight and
-// returns, so a lost completion can never hang the GPU.
+// Every wait is bounded: after about two seconds of failed polls the kernel
+// records an error code, waits (bounded again) for its own copies still in
+// flight and returns, so a lost completion can never hang the GPU.
 #pragma once
 #include "common.cuh"
 
 namespace f3r {
 
-constexpr long long kSpinLimit = 1LL << 24;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at the 2.07 GHz SM clock
 constexpr int kMaxExtra = kMaxDots + 1;
 enum { ERR_STAGE_TIMEOUT = 1 };
 
@@ -61,15 +62,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait; false after kSpinLimit polls
+// Bounded, warp-uniform wait for phase `parity` of a barrier: every lane
+// polls (so each lane acquires the completed phase), the warp leaves together
+// once all lanes saw it, and gives up after kWaitCycles of lane 0's clock.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+    const long long t0 = __shfl_sync(0xffffffffu, (long long)clock64(), 0);
+    for (;;) {
+        const bool ok = mbar_try_wait(bar, parity);
+        if (__all_sync(0xffffffffu, ok)) return true;
+        const long long now = __shfl_sync(0xffffffffu, (long long)clock64(), 0);
+        if (now - t0 > kWaitCycles) return false;
+    }
 }
 
-// Extra row-aligned segments staged with each slice: rows [32 s, 32 s + 32)
-// of `count` vectors base + l * ld (element size esize bytes).
+// Extra row-aligned segments staged with each tile: rows [256 t, 256 t + 256)
+// of `count` vectors base + l * ld (element size esize bytes; ld a multiple
+// of 256 so that every tile's rows exist).
 struct Extra {
     const void *base = nullptr;
     int count = 0;
@@ -77,33 +85,41 @@ struct Extra {
     int esize = 4;
 };
 
-// Shared-memory layout of one stage for a slice of width w:
-//   [col: 32 w int32][val: 32 w TA][extra l: 32 elements each]
+constexpr int kTileSlices = kWarps;              // one slice per warp of the block
+constexpr int kTileRows = kTileSlices * kSlice;  // 256 rows per tile
+
+// What one warp sees of its slice in a staged tile.
 template <class TA> struct StageView {
-    const int *col;
+    const int *col;     // 32 w entries, column-major within the slice
     const TA *val;
-    const char *extra;
+    const char *extra;  // extra l of the whole tile at extra + l * 256 * esize
     int w;
     int esize;
+    int row0;           // row of lane 0 inside the tile (32 * warp)
     template <class T> __device__ const T *ext(int l) const {
-        return reinterpret_cast<const T *>(extra + (size_t)l * kSlice * esize);
+        return reinterpret_cast<const T *>(extra + (size_t)l * kTileRows * esize) + row0;
     }
 };
 
-// Per-warp ring of S stages over the warp's slices.  `ring` points to this
-// warp's S * stage_bytes of dynamic shared memory, `bars` to its S mbarriers.
-// body(s, view) is called by all 32 lanes for every slice in order.
+// Block-level ring of S stages over a contiguous range of tiles.  Thread 0
+// fills a stage with one bulk copy of the tile's column indices, one of its
+// values and one per extra vector; all warps wait on the stage's mbarrier,
+// warp w processes slice w of the tile, and after a block-wide barrier the
+// stage is refilled with the tile S ahead.  body(s, view) runs on all lanes of
+// the warp owning slice s.  The stop decision after a failed wait is
+// block-uniform (__syncthreads_or), so no warp is left at a barrier.
 template <class TA, int S, class Body>
-__device__ __forceinline__ bool staged_slices(const Sell &A, const TA *__restrict__ val, int first, int stride,
-                                              char *ring, int stage_bytes, uint64_t *bars, Extra ex, int *err,
-                                              Body body) {
-    const int lane = threadIdx.x & 31;
-    auto issue = [&](int s, int st) {
-        const int b0 = __ldg(A.sptr + s), b1 = __ldg(A.sptr + s + 1);
-        const int w = (b1 - b0) >> 5;
-        const uint32_t colb = (uint32_t)w * kSlice * 4u;
-        const uint32_t valb = (uint32_t)w * kSlice * (uint32_t)sizeof(TA);
-        const uint32_t extb = (uint32_t)kSlice * ex.esize;
+__device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict__ val, int tile_begin,
+                                             int tile_end, char *ring, int stage_bytes, uint64_t *bars, Extra ex,
+                                             int *err, Body body) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    auto issue = [&](int t, int st) {
+        const int s0 = t * kTileSlices;
+        const int s1 = min(s0 + kTileSlices, A.nslices);
+        const int b0 = __ldg(A.sptr + s0), b1 = __ldg(A.sptr + s1);
+        const uint32_t colb = (uint32_t)(b1 - b0) * 4u;
+        const uint32_t valb = (uint32_t)(b1 - b0) * (uint32_t)sizeof(TA);
+        const uint32_t extb = (uint32_t)kTileRows * ex.esize;
         const uint32_t bar = smem_u32(bars + st);
         const uint32_t dst = smem_u32(ring + (size_t)st * stage_bytes);
         fence_proxy_async();  // earlier generic reads of this stage before the async refill
@@ -114,55 +130,56 @@ __device__ __forceinline__ bool staged_slices(const Sell &A, const TA *__restric
         }
         for (int l = 0; l < ex.count; ++l)
             bulk_g2s(dst + colb + valb + l * extb,
-                     (const char *)ex.base + ((size_t)l * ex.ld + (size_t)s * kSlice) * ex.esize, extb, bar);
+                     (const char *)ex.base + ((size_t)l * ex.ld + (size_t)t * kTileRows) * ex.esize, extb, bar);
     };
-    if (lane == 0) {
+    if (threadIdx.x == 0) {
         for (int st = 0; st < S; ++st) mbar_init(smem_u32(bars + st), 1);
         fence_mbar_init();
     }
-    __syncwarp();
-    if (lane == 0)
-        for (int st = 0; st < S; ++st) {
-            const int s = first + st * stride;
-            if (s < A.nslices) issue(s, st);
-        }
-    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int st = 0; st < S; ++st)
+            if (tile_begin + st < tile_end) issue(tile_begin + st, st);
     bool ok = true;
     int k = 0;
-    for (int s = first; s < A.nslices; s += stride, ++k) {
+    for (int t = tile_begin; t < tile_end; ++t, ++k) {
         const int st = k % S;
-        const uint32_t parity = (uint32_t)((k / S) & 1);
-        if (!mbar_wait(smem_u32(bars + st), parity)) {
+        const bool got = mbar_wait(smem_u32(bars + st), (uint32_t)((k / S) & 1));
+        if (__syncthreads_or(got ? 0 : 1)) {
             ok = false;
             break;
         }
-        const char *base = ring + (size_t)st * stage_bytes;
-        const int b0 = __ldg(A.sptr + s), b1 = __ldg(A.sptr + s + 1);
-        StageView<TA> v;
-        v.w = (b1 - b0) >> 5;
-        v.col = reinterpret_cast<const int *>(base);
-        v.val = reinterpret_cast<const TA *>(base + (size_t)v.w * kSlice * 4);
-        v.extra = base + (size_t)v.w * kSlice * (4 + sizeof(TA));
-        v.esize = ex.esize;
-        body(s, v);
-        __syncwarp();
-        const int sn = s + S * stride;
-        if (lane == 0 && sn < A.nslices) issue(sn, st);
-        __syncwarp();
+        const int s = t * kTileSlices + warp;
+        if (s < A.nslices) {
+            const char *base = ring + (size_t)st * stage_bytes;
+            const int bt = __ldg(A.sptr + t * kTileSlices);
+            const int tile_nnz = __ldg(A.sptr + min(t * kTileSlices + kTileSlices, A.nslices)) - bt;
+            const int b0 = __ldg(A.sptr + s), b1 = __ldg(A.sptr + s + 1);
+            StageView<TA> v;
+            v.w = (b1 - b0) >> 5;
+            v.col = reinterpret_cast<const int *>(base) + (b0 - bt);
+            v.val = reinterpret_cast<const TA *>(base + (size_t)tile_nnz * 4) + (b0 - bt);
+            v.extra = base + (size_t)tile_nnz * (4 + sizeof(TA));
+            v.esize = ex.esize;
+            v.row0 = warp * kSlice;
+            body(s, v);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && t + S < tile_end) issue(t + S, st);
     }
     if (!ok) {
-        // record the failure, then drain this warp's copies still in flight (bounded)
-        if (lane == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
-        int kk = k;
-        for (int s = first + k * stride; s < A.nslices && kk < k + S; s += stride, ++kk)
+        // record the failure, then drain the copies still in flight (bounded waits)
+        if (threadIdx.x == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
+        for (int kk = k; kk < k + S && tile_begin + kk < tile_end; ++kk)
             mbar_wait(smem_u32(bars + kk % S), (uint32_t)((kk / S) & 1));
     }
+    (void)lane;
     return ok;
 }
 
-// stage size in bytes for slices of width up to wmax
+// stage size in bytes for tiles of slices up to wmax wide
 __host__ __device__ inline int stage_bytes_for(int wmax, int asize, int n_extra, int esize) {
-    const int b = wmax * kSlice * (4 + asize) + n_extra * kSlice * esize;
+    const int b = kTileSlices * wmax * kSlice * (4 + asize) + n_extra * kTileRows * esize;
     return (b + 15) / 16 * 16;
 }
 

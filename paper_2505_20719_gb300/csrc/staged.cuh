@@ -1,0 +1,154 @@
+// SELL kernels whose matrix slices are staged into shared memory by bulk
+// asynchronous copies (stage.cuh): the inner-level SpMV with fused CGS dot
+// products, the fused m4 = 2 Richardson call, the stand-alone SpMV and the
+// outer fp64 SpMV.  Each lane still sums its row in CSR order with fused
+// multiply-add, so results equal the unstaged kernels bit for bit.
+//
+// Dynamic shared memory per block: [S mbarriers, padded to 256 B]
+// [ring of S stages of `stage_bytes`].  Block b owns the contiguous tiles
+// [b * per, (b + 1) * per), per = ceil(tiles / gridDim.x).
+#pragma once
+#include "kernels.cuh"
+#include "rich.cuh"
+#include "stage.cuh"
+
+namespace f3r {
+
+constexpr int kBarBytes = 256;
+
+struct StageCfg {
+    int stage_bytes;
+    int *err;
+};
+
+__device__ __forceinline__ char *block_ring(char *dsm) { return dsm + kBarBytes; }
+__device__ __forceinline__ uint64_t *block_bars(char *dsm) { return reinterpret_cast<uint64_t *>(dsm); }
+
+// this block's contiguous range of tiles
+__device__ __forceinline__ int2 tile_range(const Sell &A) {
+    const int ntiles = (A.nslices + kTileSlices - 1) / kTileSlices;
+    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
+    const int b = blockIdx.x * per;
+    return make_int2(min(b, ntiles), min(b + per, ntiles));
+}
+
+// one row of a staged slice: sum_k a_k x(c_k) in CSR order
+template <class TC, class TA, class GX>
+__device__ __forceinline__ TC staged_row(const StageView<TA> &v, int lane, GX gx) {
+    TC acc = (TC)0;
+#pragma unroll 8
+    for (int k = 0; k < v.w; ++k) {
+        const int c = v.col[k * kSlice + lane];
+        const TA a = v.val[k * kSlice + lane];
+        if (c >= 0) acc = fma_rn(to_c<TC>(a), gx(c), acc);
+    }
+    return acc;
+}
+
+// w = A Z[j] (times the row scale), hA = V[0..j]^T w; V rows staged with the slice
+template <class TA, class T, int S, int MAXD>
+__global__ void __launch_bounds__(kBlock) k_spmv_dots_st(Sell A, const TA *__restrict__ val,
+                                                         const float *__restrict__ rs, LevelDev<T> L, int j,
+                                                         GridRed<T> gr, StageCfg cfg) {
+    if (stopped(L.flags, L.depth)) return;
+    extern __shared__ __align__(128) char dsm[];
+    const int lane = threadIdx.x & 31;
+    const T *__restrict__ x = L.Z + (size_t)j * L.ld;
+    T acc[MAXD];
+#pragma unroll
+    for (int l = 0; l < MAXD; ++l) acc[l] = (T)0;
+    Extra ex;
+    ex.base = L.V;
+    ex.count = j + 1;
+    ex.ld = L.ld;
+    ex.esize = sizeof(T);
+    const int2 tr = tile_range(A);
+    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_bars(dsm), ex, cfg.err,
+                        [&](int s, const StageView<TA> &v) {
+                             T y = staged_row<T>(v, lane, [&](int c) { return __ldg(x + c); });
+                             const int i = s * kSlice + lane;
+                             if (rs) y = mul_rn(y, (T)__ldg(rs + i));
+                             if (i < L.n) {
+                                 L.w[i] = y;
+#pragma unroll
+                                 for (int l = 0; l < MAXD; ++l)
+                                     if (l <= j) acc[l] = fma_rn(v.template ext<T>(l)[lane], y, acc[l]);
+                             }
+                         });
+    grid_reduce<T, MAXD>(acc, j + 1, false, gr, [&](T *res) {
+        T *hA = L.hA();
+        for (int l = 0; l <= j; ++l) hA[l] = res[l];
+    });
+}
+
+// fused plain Richardson call with m4 = 2 (see k_rich2)
+template <class TA, class VS, class TC, class TP, int S>
+__global__ void __launch_bounds__(kBlock) k_rich2_st(Sell A, const TA *__restrict__ val, const float *__restrict__ rs,
+                                                     const VS *__restrict__ v, const VS *__restrict__ mv, TP *out,
+                                                     const TP *par_misc, RichDev<TC> R, const int *flags,
+                                                     int check_depth, int n, StageCfg cfg) {
+    if (stopped(flags, check_depth)) return;
+    extern __shared__ __align__(128) char dsm[];
+    const int lane = threadIdx.x & 31;
+    const TC w1 = R.omega[0], w2 = R.omega[1];
+    const TP inv_sigma = par_misc[MS_INV_SIGMA];
+    const int2 tr = tile_range(A);
+    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_bars(dsm), Extra(), cfg.err,
+                        [&](int s, const StageView<TA> &st) {
+                             TC acc = staged_row<TC>(st, lane, [&](int c) {
+                                 return rnd<VS>(fma_rn(w1, mul_rn(to_c<TC>(__ldg(mv + c)), to_c<TC>(__ldg(v + c))),
+                                                       (TC)0));
+                             });
+                             const int i = s * kSlice + lane;
+                             if (rs) acc = mul_rn(acc, (TC)__ldg(rs + i));
+                             if (i < n) {
+                                 const TC vi = to_c<TC>(v[i]), mi = to_c<TC>(mv[i]);
+                                 const TC z1 = rnd<VS>(fma_rn(w1, mul_rn(mi, vi), (TC)0));
+                                 const TC ri = rnd<VS>(sub_rn(vi, acc));
+                                 const TC z2 = rnd<VS>(fma_rn(w2, mul_rn(mi, ri), z1));
+                                 out[i] = mul_rn((TP)z2, inv_sigma);
+                             }
+                         });
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicAdd(R.counters + 0, 2ull);
+        atomicAdd(R.counters + 1, 1ull);
+    }
+}
+
+// stand-alone y = A x
+template <class TA, class TX, class TY, int S>
+__global__ void __launch_bounds__(kBlock) k_spmv_st(Sell A, const TA *__restrict__ val, const float *__restrict__ rs,
+                                                    const TX *__restrict__ x, TY *y, StageCfg cfg) {
+    extern __shared__ __align__(128) char dsm[];
+    const int lane = threadIdx.x & 31;
+    const int2 tr = tile_range(A);
+    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_bars(dsm), Extra(), cfg.err,
+                        [&](int s, const StageView<TA> &st) {
+                             TY acc = staged_row<TY>(st, lane, [&](int c) { return to_c<TY>(__ldg(x + c)); });
+                             const int i = s * kSlice + lane;
+                             if (rs) acc = mul_rn(acc, (TY)__ldg(rs + i));
+                             if (i < A.n) y[i] = acc;
+                         });
+}
+
+// outer level: Z[j] = z (the inner nest's output) and w = A z, original fp64 A
+template <int S>
+__global__ void __launch_bounds__(kBlock) k_outer_spmv_st(Sell A, const double *__restrict__ a, LevelDev<double> L,
+                                                          const double *__restrict__ z, StageCfg cfg) {
+    extern __shared__ __align__(128) char dsm[];
+    const int lane = threadIdx.x & 31;
+    const int j = *L.jptr;
+    double *zj = L.Z + (size_t)j * L.ld;
+    const int2 tr = tile_range(A);
+    staged_tiles<double, S>(A, a, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_bars(dsm), Extra(), cfg.err,
+                            [&](int s, const StageView<double> &st) {
+                                 const double y = staged_row<double>(st, lane, [&](int c) { return __ldg(z + c); });
+                                 const int i = s * kSlice + lane;
+                                 if (i < L.n) {
+                                     L.w[i] = y;
+                                     zj[i] = z[i];
+                                 }
+                             });
+}
+
+}  // namespace f3r
