@@ -34,6 +34,7 @@ WORKLOADS = {
                       "symmetric diagonal scaling, fp16 inner storage, Jacobi M, F3R (100,8,4,2), c=64, tol 1e-9",
     "convdiff27_160": "nonsymmetric 3-D 27-point convection-diffusion 160^3, cell Peclet in [0.1,10]",
     "poisson2d_64": "2-D 5-point Poisson 64x64, Jacobi M unscaled",
+    "batched64": "64 uneven 2-D/3-D diffusion systems (n log-uniform in [1e4, 5e5]), 1-8 right-hand sides each",
 }
 
 
@@ -151,6 +152,109 @@ def cpu_baseline(prob, kind, outer_iters, max_seconds=25.0):
                       f"({dt:.1f} s), scaled linearly to the full solve"}
 
 
+def level_error_report(prob, rp, ci, va, ds, dev, stream):
+    """Error of one call of each inner level (F_m2, F_m3, R_m4) in fp16, bf16
+    and fp32 storage against the same call computed entirely in fp64, on the
+    same unit input vector: ||z - z64|| / ||z64|| and the level's own
+    residual reduction ||v - A^ z|| / ||v|| (A^ the fp64 scaled matrix)."""
+    import torch
+    import scipy.sparse as sp
+    from paper_2505_20719_gb300 import f3r
+    n = prob.n
+    v = torch.randn(n, device=dev, dtype=torch.float64, generator=torch.Generator(device=dev).manual_seed(5))
+    v /= v.norm()
+    ref = f3r.Solver(rp, ci, va, f3r.preset("fp64-F3R", diag_scale=ds), stream=stream)
+    ah = sp.csr_matrix((ref.export(1, prob.nnz), prob.colidx, prob.rowptr), shape=(n, n))
+    out = {}
+    z64 = {}
+    for level in (1, 2, 3):
+        ref.set_rich_state([1.0, 1.0], 2)
+        z = torch.empty(n, device=dev, dtype=torch.float64)
+        ref.apply(level, v, z, stream=stream)
+        z64[level] = z.cpu().numpy()
+    vh = v.cpu().numpy()
+    for kind in ("fp16-F3R", "bf16-F3R", "fp32-F3R"):
+        s = f3r.Solver(rp, ci, va, f3r.preset(kind, diag_scale=ds), stream=stream)
+        row = {}
+        for level, name in ((1, "F_m2"), (2, "F_m3"), (3, "R_m4")):
+            s.set_rich_state([1.0, 1.0], 2)
+            v32 = v.to(torch.float32)
+            z = torch.empty(n, device=dev, dtype=torch.float32)
+            s.apply(level, v32, z, stream=stream)
+            zh = z.double().cpu().numpy()
+            v32h = v32.double().cpu().numpy()
+            row[name] = {"rel_err_vs_fp64": float(np.linalg.norm(zh - z64[level]) / np.linalg.norm(z64[level])),
+                         "level_residual": float(np.linalg.norm(v32h - ah @ zh) / np.linalg.norm(v32h)),
+                         "fp64_level_residual": float(np.linalg.norm(vh - ah @ z64[level]) / np.linalg.norm(vh))}
+        out[kind] = row
+        s.close()
+    ref.close()
+    return out
+
+
+def run_batched(args):
+    """Throughput of the batched solver (one persistent launch for all
+    instances) against solving the same instances one by one with the
+    single-system solver on the same GPU."""
+    import torch
+    from paper_2505_20719_gb300 import f3r
+    from problems import generators as G
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    batch = G.batched_diffusion_systems()
+    systems = [(T(p.rowptr), T(p.colidx), T(p.val), B.shape[0]) for p, B in batch]
+    Bs, Xs = [], []
+    for p, B in batch:
+        for r in range(B.shape[0]):
+            Bs.append(T(B[r]))
+            Xs.append(torch.zeros(p.n, dtype=torch.float64, device=dev))
+    bs = f3r.BatchedSolver(systems, f3r.default_params())
+    chosen = bs.autotune(Bs, Xs)
+    times = []
+    for it in range(args.warmup + args.steps):
+        for x in Xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        code, res = bs.solve(Bs, Xs)
+        e1.record()
+        e1.synchronize()
+        if it >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    ok = sum(1 for r in res if r.status == 0)
+    # sequential: the single-system solver, one instance after another
+    seq_ms = 0.0
+    q = 0
+    for p, B in batch:
+        s = f3r.Solver(T(p.rowptr), T(p.colidx), T(p.val), f3r.default_params())
+        for r in range(B.shape[0]):
+            x = torch.zeros(p.n, dtype=torch.float64, device=dev)
+            s.solve(Bs[q], x)  # warm (graphs)
+            x.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            s.solve(Bs[q], x)
+            e1.record()
+            e1.synchronize()
+            seq_ms += e0.elapsed_time(e1)
+            q += 1
+        s.close()
+    ninst = len(Bs)
+    out = {"metric": "batched F3R throughput (systems x right-hand sides solved to 1e-9 per second)",
+           "value": ninst / (ms / 1e3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "batched64", "desc": WORKLOADS["batched64"], "instances": ninst,
+                      "rows_total": int(sum(p.n * B.shape[0] for p, B in batch)), "cluster": chosen},
+           "converged": ok, "max_outer_iters": max(r.outer_iters for r in res),
+           "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+           "device_bytes": bs.device_bytes}
+    print(json.dumps(out))
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -201,6 +305,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched64":
+        return run_batched(args)
 
     import torch
     from paper_2505_20719_gb300 import f3r
@@ -309,6 +415,9 @@ def main():
             "algorithmic_bytes_per_launch": sp_bytes}
     spmv["frac"] = spmv["achieved"] / hbm
 
+    # ---- per-level error of the low-precision levels against the fp64 path (same inputs)
+    level_errors = level_error_report(prob, rp, ci, va, ds, dev, stream)
+
     # ---- comparators on the same GPU (one solve each)
     comparators = {}
     if not args.no_comparators:
@@ -360,7 +469,7 @@ def main():
                    "l2": "flushed (256 MiB write) before every timed solve"},
         "outer_iters": last.outer_iters, "rel_res_true": true_rel, "status": f3r.STATUS.get(last.status),
         "roofline": roofline, "spmv_fp16": spmv, "kernels": prof, "comparators": comparators,
-        "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        "level_errors": level_errors, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         "device_bytes": s.device_bytes,
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

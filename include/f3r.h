@@ -50,7 +50,7 @@ typedef enum {
 } f3r_status;
 
 enum { F3R_F64 = 0, F3R_F32 = 1, F3R_F16 = 2, F3R_BF16 = 3 };
-enum { F3R_PC_IDENTITY = 0, F3R_PC_JACOBI = 1 };
+enum { F3R_PC_IDENTITY = 0, F3R_PC_JACOBI = 1, F3R_PC_LEARNED = 2 };
 
 /* Solver configuration.  f3r_default_params gives F3R with the paper's
  * defaults: (m1, m2, m3, m4) = (100, 8, 4, 2), c = 64, Table 1 precisions,
@@ -65,7 +65,9 @@ typedef struct {
     int rich_a_prec;    /* precision of A inside Richardson */
     int rich_v_prec;    /* precision of Richardson vectors: F16, BF16, F32 or F64 */
     int m_prec;         /* storage precision of M */
-    int precond;        /* F3R_PC_JACOBI (M = diag(A^)^-1) or F3R_PC_IDENTITY */
+    int precond;        /* F3R_PC_JACOBI (M = diag(A^)^-1), F3R_PC_IDENTITY, or F3R_PC_LEARNED
+                           (the learned net as M inside an fp16 Richardson level; Jacobi
+                           until f3r_learned_load is called) */
     int c;              /* weight-update period of Algorithm 1 (>= 1) */
     double omega_fixed; /* > 0: fixed Richardson weight, no adaptive update */
     int diag_scale;     /* 1: inner nest works on A^ = D^-1/2 A D^-1/2, D = |diag A| (Sec. 5) */
@@ -159,6 +161,97 @@ f3r_status f3r_profile_enable(f3r_ctx *ctx, int enable);
 f3r_status f3r_profile_get(f3r_ctx *ctx, int slot, int64_t *launches, double *total_ms);
 int f3r_profile_slots(void);
 const char *f3r_profile_slot_name(int slot);
+
+/* ------------------------------------------------------------ learned M
+ * Learned preconditioner M_theta (project addition; the paper's M is an
+ * algebraic preconditioner, Sec. 3): a 3-layer message-passing network of
+ * width 32 over the graph of A^ (fp16 copy), bf16 weights, activations and
+ * messages, fp32 accumulation (mma.sync bf16 tensor-core products), with the
+ * s-normalisation that makes it homogeneous for powers of two:
+ *   h0 = relu(e r~ + b0), g = offdiag(A^) h, h = relu([h|g][Ws|Wm]^T + b) (x3),
+ *   z = s (omega_j r~ + wo . h),  r~ = r / s,  s = 2^ceil(log2 max|r|).
+ * Parameters are a flat fp32 vector of F3R_LEARNED_NPARAMS values in the order
+ * e[32], b0[32], Ws[3][32][32], Wm[3][32][32], b[3][32], wo[32], omega_j.
+ * Training needs a symmetric A^ and a context holding the fp16 copy of A^. */
+#define F3R_LEARNED_NPARAMS 6337
+
+/* Load parameters (host or device, fp32) into the context; `train` = 1 also
+ * allocates the training buffers (activations of all layers).  With
+ * precond = F3R_PC_LEARNED the solver then uses the net as M. */
+f3r_status f3r_learned_load(f3r_ctx *ctx, const float *params, int train);
+/* Copy the current fp32 parameters to host memory `out` (NPARAMS floats). */
+f3r_status f3r_learned_get(f3r_ctx *ctx, float *out);
+/* z = M_theta(r), r and z device fp32 vectors of n values. */
+f3r_status f3r_learned_apply(f3r_ctx *ctx, const float *r, float *z, void *stream);
+/* Mean loss over P samples of ||M_theta(r_p) - e_p||^2 / ||e_p||^2 and its
+ * gradient (R, E device fp32, P x n row-major); loss and grad (NPARAMS) are
+ * host outputs, either may be NULL. */
+f3r_status f3r_learned_loss_grad(f3r_ctx *ctx, const float *R, const float *E, int P, float *loss, float *grad,
+                                 void *stream);
+/* Adam training: `steps` steps, each on a mini-batch of `batch` consecutive
+ * samples (cycling through the P pairs), learning rate lr; loss_hist (host,
+ * optional, `steps` floats) receives each step's mini-batch loss. */
+f3r_status f3r_learned_train(f3r_ctx *ctx, const float *R, const float *E, int P, int steps, int batch, float lr,
+                             float *loss_hist, void *stream);
+
+/* ---------------------------------------------------------------- batched
+ * Many systems, each with one or more right-hand sides, solved by F3R in a
+ * single persistent kernel launch (project addition; the paper solves one
+ * system at a time).  Each (system, right-hand side) instance is solved
+ * entirely on the device by one thread-block cluster with the default F3R
+ * precision schedule (Table 1): fp64 FGMRES(m1) with its convergence test
+ * and restarts, fp32 FGMRES(m2), FGMRES(m3) with fp16 A, fp16 Richardson
+ * R_2 with adaptive weights (Algorithm 1), Jacobi M.  Clusters take instances
+ * largest-first from an atomic work queue. */
+typedef struct f3r_batch f3r_batch;
+
+typedef struct {
+    int32_t n;               /* rows */
+    int64_t nnz;
+    const int32_t *rowptr;   /* CSR, host or device pointers (copied at setup) */
+    const int32_t *colidx;
+    const double *val;
+    int32_t nrhs;            /* right-hand sides of this system (>= 1) */
+} f3r_system_desc;
+
+typedef struct {
+    int status;              /* f3r_status of this instance */
+    int outer_iters;
+    int restarts;
+    double rel_res_true;     /* final ||b - A x|| / ||b|| */
+    int64_t m_applies;
+    int64_t r_calls;
+    double t_solve_ms;       /* device time of the whole batched launch */
+    int system, rhs;         /* which instance */
+} f3r_batch_result;
+
+/* Set up all systems (setup of each matrix as in f3r_setup) and the
+ * per-instance workspace.  params must keep the default precision schedule
+ * (nlevels 3, m4 = 2, fp16 A at level 2 and in R, no row scaling); m1, m2,
+ * m3, c, tol, max_outer, cgs_passes, omega_fixed and scale_cast are honoured.
+ * Errors: F3R_ERR_ARG, F3R_ERR_UNSUPPORTED, F3R_ERR_NOMEM, F3R_ERR_CUDA. */
+f3r_status f3r_setup_batched(f3r_batch **batch, int nsys, const f3r_system_desc *systems,
+                             const f3r_params *params, void *stream);
+
+/* Solve every instance: B[q] and X[q] are device pointers (n of system q's
+ * system fp64 values) for instance q, instances numbered system by system
+ * and right-hand side by right-hand side; X[q] holds x0 on entry.  One
+ * kernel launch; res (optional, one entry per instance) receives each
+ * instance's result.  Returns F3R_OK if every instance converged, else the
+ * status of the first instance that did not. */
+f3r_status f3r_solve_batched(f3r_batch *batch, const double *const *B, double *const *X, f3r_batch_result *res,
+                             void *stream);
+
+/* Thread-block cluster size of the batched launch (1, 2, 4 or 8; default 8). */
+f3r_status f3r_batched_set_cluster(f3r_batch *batch, int cluster_size);
+/* Autotuner: times one outer iteration of the whole batch (from x0 = 0) for
+ * cluster sizes 1, 2, 4 and 8 and keeps the fastest (written to *chosen if
+ * not NULL).  B and X as in f3r_solve_batched; X is zero on return. */
+f3r_status f3r_batched_autotune(f3r_batch *batch, const double *const *B, double *const *X, int *chosen,
+                                void *stream);
+int f3r_batched_instances(const f3r_batch *batch);
+int64_t f3r_batched_device_bytes(const f3r_batch *batch);
+void f3r_destroy_batched(f3r_batch *batch);
 
 /* Residual without device allocation (no counterpart in the paper).
  *

@@ -1,0 +1,968 @@
+// Batched F3R: many systems and right-hand sides in one persistent launch.
+//
+// Every (system, right-hand side) instance is solved entirely on the device
+// by one thread-block cluster ("team"): the outer fp64 FGMRES(m1) with its
+// convergence test and restarts, the fp32 FGMRES(m2), the FGMRES(m3) with
+// fp16 A and the fp16 Richardson R_2 with adaptive weights (Sec. 4.2,
+// Table 1, Algorithm 1) -- the same arithmetic as the single-system path.
+// Kernel boundaries become cluster barriers (barrier.cluster), reductions sum
+// per-block partials in distributed shared memory in a fixed rank order, and
+// the small Givens / least-squares state of the inner levels is kept, and
+// updated identically, in every block of the team.  Clusters take instances
+// from an atomic work queue ordered by size (largest first).  All control
+// decisions derive from values every block of a team holds identically, so
+// every block reaches every cluster barrier.
+//
+// Data written inside the launch is read with ld.global.cg (L2), never through
+// the non-coherent read-only path.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "ctx.h"
+#include "kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace f3r {
+namespace bt {
+
+constexpr int kBT = 512;          // threads per block
+constexpr int kBW = kBT / 32;     // warps per block
+constexpr int kMaxCluster = 8;
+constexpr int kRedMax = 16;       // sums per team reduction
+
+struct Sys {
+    int n, nslices;
+    const int *sptr, *col;
+    const double *a64;   // original A
+    const float *a32;    // A^ fp32
+    const h16 *a16;      // A^ fp16
+    const double *dsc;   // D^-1/2
+    const h16 *m16;      // Jacobi M
+};
+
+struct Inst {
+    int sys;
+    const double *b;
+    double *x;
+    double *V1, *Z1, *w1, *H1;  // H1: (m1+1) m1 + 4 m1 + 2 doubles (H, cs, sn, g, y)
+    float *V2, *Z2, *w2;
+    float *V3, *Z3, *w3;
+    h16 *rin, *rz, *rr;
+    int ld;
+};
+
+struct Out {
+    int status, outer_iters, restarts;
+    double rel;
+    long long m_applies, r_calls;
+};
+
+struct BP {
+    int m1, m2, m3, c, max_outer, cgs_passes, scale_cast;
+    double tol;
+    float omega_fixed;
+};
+
+// per-level least-squares state of an inner level, replicated in every block
+struct LS {
+    float H[(kMaxInnerM + 1) * kMaxInnerM];
+    float cs[kMaxInnerM], sn[kMaxInnerM], g[kMaxInnerM + 1], y[kMaxInnerM];
+    float hA[kMaxDots], hB[kMaxDots];
+    float beta, inv, sigma, inv_sigma;
+    int kdim, stop, nonfinite;
+};
+
+struct Shared {
+    double red_blk[kRedMax];   // this block's partial sums
+    double red_res[kRedMax];   // rank 0: the team's sums
+    double wred[kRedMax][kBW];
+    LS ls2, ls3;
+    float omega[2];
+    long long c_ntr;
+    // rank 0: outer-level decisions broadcast to the team
+    double o_inv, o_est, o_beta, o_rel;
+    int o_stop, o_kdim, o_nonfinite, inst;
+};
+
+struct Team {
+    unsigned rank, size;
+    int tid, nthr, wid, nwarps, lane;
+};
+
+__device__ __forceinline__ void team_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <class T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
+__device__ __forceinline__ h16 ldcg(const h16 *p) {
+    unsigned short u = __ldcg(reinterpret_cast<const unsigned short *>(p));
+    return __ushort_as_half(u);
+}
+
+// Deterministic team reduction of nd sums (nd <= kRedMax), or maxima where
+// is_max; every thread of the team returns the results in out[].
+template <class T>
+__device__ void team_reduce(const Team &tm, Shared &sh, T *acc, int nd, T *out, const bool *is_max = nullptr) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = 0; d < nd; ++d) {
+        const bool mx = is_max && is_max[d];
+        T v = mx ? warp_max(acc[d]) : warp_sum(acc[d]);
+        if (lane == 0) sh.wred[d][warp] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nd) {
+        const int d = threadIdx.x;
+        const bool mx = is_max && is_max[d];
+        T s = (T)sh.wred[d][0];
+        for (int w = 1; w < kBW; ++w) s = mx ? fmax(s, (T)sh.wred[d][w]) : add_rn(s, (T)sh.wred[d][w]);
+        sh.red_blk[d] = (double)s;
+    }
+    team_sync();
+    if (tm.rank == 0 && threadIdx.x < nd) {
+        const int d = threadIdx.x;
+        const bool mx = is_max && is_max[d];
+        T s = (T)0;
+        for (unsigned r = 0; r < tm.size; ++r) {
+            const double *rb = cl.map_shared_rank(sh.red_blk, r);
+            s = (r == 0) ? (T)rb[d] : (mx ? fmax(s, (T)rb[d]) : add_rn(s, (T)rb[d]));
+        }
+        sh.red_res[d] = (double)s;
+    }
+    team_sync();
+    const double *res0 = cl.map_shared_rank(sh.red_res, 0);
+    for (int d = 0; d < nd; ++d) out[d] = (T)res0[d];
+    team_sync();
+}
+
+// ---------------------------------------------------------------- Givens
+// Saad 6.5.3 update of an inner level with column j; identical in every block.
+__device__ void ls_column(LS &L, int m, int j, const float *hcol, float hn, bool last) {
+    const int ldh = m + 1;
+    bool finite = isfinite(hn);
+    for (int i = 0; i <= j; ++i) finite = finite && isfinite(hcol[i]);
+    bool ok = finite;
+    if (ok) {
+        for (int i = 0; i <= j; ++i) L.H[i + ldh * j] = hcol[i];
+        L.H[j + 1 + ldh * j] = hn;
+        for (int i = 0; i < j; ++i) {
+            const float t = add_rn(mul_rn(L.cs[i], L.H[i + ldh * j]), mul_rn(L.sn[i], L.H[i + 1 + ldh * j]));
+            L.H[i + 1 + ldh * j] = add_rn(mul_rn(-L.sn[i], L.H[i + ldh * j]), mul_rn(L.cs[i], L.H[i + 1 + ldh * j]));
+            L.H[i + ldh * j] = t;
+        }
+        const float a = L.H[j + ldh * j], b = L.H[j + 1 + ldh * j];
+        const float rho = sqrt_rn(add_rn(mul_rn(a, a), mul_rn(b, b)));
+        ok = rho > 0.0f && isfinite(rho);
+        if (ok) {
+            L.cs[j] = div_rn(a, rho);
+            L.sn[j] = div_rn(b, rho);
+            L.H[j + ldh * j] = rho;
+            L.H[j + 1 + ldh * j] = 0.0f;
+            L.g[j + 1] = mul_rn(-L.sn[j], L.g[j]);
+            L.g[j] = mul_rn(L.cs[j], L.g[j]);
+        }
+    }
+    if (!finite) L.nonfinite = 1;
+    bool stop = !ok;
+    if (ok) {
+        L.kdim = j + 1;
+        if (!(hn > 0.0f)) stop = true;
+        else L.inv = div_rn(1.0f, hn);
+    }
+    if (stop) L.stop = 1;
+    if (stop || last) {
+        const int k = L.kdim;
+        for (int r = k - 1; r >= 0; --r) {
+            float s = L.g[r];
+            for (int l = r + 1; l < k; ++l) s = fma_rn(-L.H[r + ldh * l], L.y[l], s);
+            L.y[r] = div_rn(s, L.H[r + ldh * r]);
+        }
+    }
+}
+
+__device__ __forceinline__ float pow2_scale_f(float a) { return pow2_scale_for(a); }
+
+// ----------------------------------------------------------- team kernels
+// row sum of slice row i over A (CSR order, fused multiply-add), x from gx
+template <class TC, class TA, class GX>
+__device__ __forceinline__ TC row_sum(const Sys &S, const TA *val, int s, int lane, GX gx) {
+    const int beg = __ldg(S.sptr + s) + lane;
+    const int w = (__ldg(S.sptr + s + 1) - __ldg(S.sptr + s)) >> 5;
+    TC acc = (TC)0;
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+        const int idx = beg + (k << 5);
+        const int c = __ldg(S.col + idx);
+        const TA a = __ldg(val + idx);
+        if (c >= 0) acc = fma_rn(to_c<TC>(a), gx(c), acc);
+    }
+    return acc;
+}
+
+struct Ctx2 {
+    const Team &tm;
+    Shared &sh;
+    const Sys &S;
+    const Inst &I;
+    const BP &P;
+    Out &o;
+};
+
+// Richardson call (Algorithm 1, m4 = 2) on rin (scaled by sigma) into out = z / sigma
+__device__ void rich_call(Ctx2 &C, float inv_sigma, float *out) {
+    const Team &tm = C.tm;
+    Shared &sh = C.sh;
+    const Sys &S = C.S;
+    const Inst &I = C.I;
+    const int n = S.n;
+    const bool fixed = C.P.omega_fixed > 0.0f;
+    const bool update = !fixed && (sh.c_ntr % C.P.c) == 0;
+    if (!update) {
+        const float w1 = sh.omega[0], w2 = sh.omega[1];
+        for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
+            const float acc = row_sum<float>(S, S.a16, s, tm.lane, [&](int c) {
+                return rnd<h16>(fma_rn(w1, mul_rn(to_c<float>(__ldg(S.m16 + c)), to_c<float>(ldcg(I.rin + c))), 0.0f));
+            });
+            const int i = s * kSlice + tm.lane;
+            if (i < n) {
+                const float vi = to_c<float>(ldcg(I.rin + i)), mi = to_c<float>(__ldg(S.m16 + i));
+                const float z1 = rnd<h16>(fma_rn(w1, mul_rn(mi, vi), 0.0f));
+                const float ri = rnd<h16>(sub_rn(vi, acc));
+                const float z2 = rnd<h16>(fma_rn(w2, mul_rn(mi, ri), z1));
+                out[i] = mul_rn(z2, inv_sigma);
+            }
+        }
+        C.o.m_applies += 2;
+    } else {
+        // two steps, each computing w' = (r, AMr)/(AMr, AMr) in fp32
+        const long long l_ = sh.c_ntr / C.P.c;
+        for (int k = 0; k < 2; ++k) {
+            const h16 *r = (k == 0) ? I.rin : I.rr;
+            if (k == 1) {
+                for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
+                    const float acc =
+                        row_sum<float>(S, S.a16, s, tm.lane, [&](int c) { return to_c<float>(ldcg(I.rz + c)); });
+                    const int i = s * kSlice + tm.lane;
+                    if (i < n) I.rr[i] = Store<h16>::from(sub_rn(to_c<float>(ldcg(I.rin + i)), acc));
+                }
+                team_sync();
+            }
+            float acc[2] = {0.0f, 0.0f};
+            for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
+                const float w = row_sum<float>(S, S.a16, s, tm.lane, [&](int c) {
+                    return mul_rn(to_c<float>(__ldg(S.m16 + c)), to_c<float>(ldcg(r + c)));
+                });
+                const int i = s * kSlice + tm.lane;
+                if (i < n) {
+                    acc[0] = fma_rn(to_c<float>(ldcg(r + i)), w, acc[0]);
+                    acc[1] = fma_rn(w, w, acc[1]);
+                }
+            }
+            float res[2];
+            team_reduce<float>(tm, sh, acc, 2, res);
+            const float wk = sh.omega[k];
+            const float q = div_rn(res[0], res[1]);
+            const bool ok = res[1] > 0.0f && isfinite(q);
+            const float wp = ok ? q : wk;
+            __syncthreads();
+            if (threadIdx.x == 0 && ok) {
+                const float l = (float)l_;
+                sh.omega[k] = div_rn(add_rn(mul_rn(l, wk), q), add_rn(l, 1.0f));
+            }
+            for (int i = tm.tid; i < n; i += tm.nthr) {
+                const float zp = (k == 0) ? 0.0f : to_c<float>(ldcg(I.rz + i));
+                const float z = rnd<h16>(fma_rn(wp, mul_rn(to_c<float>(__ldg(S.m16 + i)), to_c<float>(ldcg(r + i))), zp));
+                if (k == 1) out[i] = mul_rn(z, inv_sigma);
+                else I.rz[i] = Store<h16>::from(z);
+            }
+            team_sync();
+        }
+        C.o.m_applies += 2;
+    }
+    C.o.r_calls += 1;
+    __syncthreads();
+    if (threadIdx.x == 0) sh.c_ntr += 1;
+    __syncthreads();
+}
+
+// Inner FGMRES level with fp32 vectors: levels 2 (A fp32) and 3 (A fp16).
+// On entry V[0] holds the input and L.beta / L.inv / L.sigma are set (or
+// L.stop); on exit out = sum_k y_k Z[k] (fp32, or fp64 * dsc for level 2).
+template <int LEVEL>
+__device__ void inner_level(Ctx2 &C, float *V, float *Z, float *w, LS &L, int m, float *out32, double *out64) {
+    const Team &tm = C.tm;
+    Shared &sh = C.sh;
+    const Sys &S = C.S;
+    const Inst &I = C.I;
+    const int n = S.n, ld = I.ld;
+    const bool half_child = (LEVEL == 3);
+    if (!L.stop) {
+        // V[0] = x / beta; the child's input from it
+        for (int i = tm.tid; i < n; i += tm.nthr) {
+            const float v = mul_rn(ldcg(V + i), L.inv);
+            V[i] = v;
+            if (LEVEL == 2) I.V3[i] = v;
+            else I.rin[i] = Store<h16>::from(mul_rn(L.sigma, v));
+        }
+        if (LEVEL == 2) {
+            // F3 start: ||V2[0]||, max -> beta3, sigma3
+            float acc[2] = {0.0f, 0.0f};
+            for (int i = tm.tid; i < n; i += tm.nthr) {
+                const float v = ldcg(I.V3 + i);
+                acc[0] = fma_rn(v, v, acc[0]);
+                acc[1] = fmax(acc[1], fabs(v));
+            }
+            const bool mx[2] = {false, true};
+            float res[2];
+            team_reduce<float>(tm, sh, acc, 2, res, mx);
+            if (threadIdx.x == 0) {
+                LS &L3 = sh.ls3;
+                const float beta = sqrt_rn(res[0]);
+                L3.kdim = 0;
+                L3.nonfinite = isfinite(beta) ? 0 : 1;
+                L3.stop = (beta > 0.0f && isfinite(beta)) ? 0 : 1;
+                L3.beta = beta;
+                if (!L3.stop) {
+                    L3.inv = div_rn(1.0f, beta);
+                    L3.g[0] = beta;
+                    L3.sigma = C.P.scale_cast ? pow2_scale_f(mul_rn(res[1], L3.inv)) : 1.0f;
+                    L3.inv_sigma = div_rn(1.0f, L3.sigma);
+                }
+            }
+            __syncthreads();
+        } else {
+            team_sync();
+        }
+    }
+    for (int j = 0; j < m && !L.stop; ++j) {
+        // child -> Z[j]
+        if (LEVEL == 2) inner_level<3>(C, I.V3, I.Z3, I.w3, sh.ls3, C.P.m3, Z + (size_t)j * ld, nullptr);
+        else rich_call(C, L.inv_sigma, Z + (size_t)j * ld);
+        team_sync();
+        // w = A Z[j], hA = V^T w
+        const float *zj = Z + (size_t)j * ld;
+        float acc[kRedMax];
+        for (int l = 0; l < kRedMax; ++l) acc[l] = 0.0f;
+        for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
+            float y = (LEVEL == 2) ? row_sum<float>(S, S.a32, s, tm.lane, [&](int c) { return ldcg(zj + c); })
+                                   : row_sum<float>(S, S.a16, s, tm.lane, [&](int c) { return ldcg(zj + c); });
+            const int i = s * kSlice + tm.lane;
+            if (i < n) {
+                w[i] = y;
+                for (int l = 0; l <= j; ++l) acc[l] = fma_rn(ldcg(V + (size_t)l * ld + i), y, acc[l]);
+            }
+        }
+        float hA[kRedMax], hB[kRedMax];
+        team_reduce<float>(tm, sh, acc, j + 1, hA);
+        const float *hl = hA;
+        if (C.P.cgs_passes == 2) {
+            for (int l = 0; l < kRedMax; ++l) acc[l] = 0.0f;
+            for (int i = tm.tid; i < n; i += tm.nthr) {
+                float wi = ldcg(w + i);
+                float v[kRedMax];
+                for (int l = 0; l <= j; ++l) {
+                    v[l] = ldcg(V + (size_t)l * ld + i);
+                    wi = fma_rn(-hA[l], v[l], wi);
+                }
+                w[i] = wi;
+                for (int l = 0; l <= j; ++l) acc[l] = fma_rn(v[l], wi, acc[l]);
+            }
+            team_reduce<float>(tm, sh, acc, j + 1, hB);
+            hl = hB;
+        }
+        float a2[2] = {0.0f, 0.0f};
+        for (int i = tm.tid; i < n; i += tm.nthr) {
+            float wi = ldcg(w + i);
+            for (int l = 0; l <= j; ++l) wi = fma_rn(-hl[l], ldcg(V + (size_t)l * ld + i), wi);
+            w[i] = wi;
+            a2[0] = fma_rn(wi, wi, a2[0]);
+            a2[1] = fmax(a2[1], fabs(wi));
+        }
+        const bool mx[2] = {false, true};
+        float r2[2];
+        team_reduce<float>(tm, sh, a2, 2, r2, mx);
+        if (threadIdx.x == 0) {
+            float hcol[kRedMax];
+            for (int l = 0; l <= j; ++l) hcol[l] = (C.P.cgs_passes == 2) ? add_rn(hA[l], hB[l]) : hA[l];
+            const float hn = sqrt_rn(r2[0]);
+            ls_column(L, m, j, hcol, hn, j == m - 1);
+            if (half_child && hn > 0.0f && C.P.scale_cast) {
+                L.sigma = pow2_scale_f(mul_rn(r2[1], L.inv));
+                L.inv_sigma = div_rn(1.0f, L.sigma);
+            } else {
+                L.sigma = 1.0f;
+                L.inv_sigma = 1.0f;
+            }
+        }
+        __syncthreads();
+        if (L.stop || j == m - 1) break;
+        // V[j+1] = w / ||w||; the child's next input
+        float b3[2] = {0.0f, 0.0f};
+        for (int i = tm.tid; i < n; i += tm.nthr) {
+            const float v = mul_rn(ldcg(w + i), L.inv);
+            V[(size_t)(j + 1) * ld + i] = v;
+            if (LEVEL == 2) {
+                I.V3[i] = v;
+                b3[0] = fma_rn(v, v, b3[0]);
+                b3[1] = fmax(b3[1], fabs(v));
+            } else {
+                I.rin[i] = Store<h16>::from(mul_rn(L.sigma, v));
+            }
+        }
+        if (LEVEL == 2) {
+            float r3[2];
+            team_reduce<float>(tm, sh, b3, 2, r3, mx);
+            if (threadIdx.x == 0) {
+                LS &L3 = sh.ls3;
+                const float beta = sqrt_rn(r3[0]);
+                L3.kdim = 0;
+                L3.nonfinite = isfinite(beta) ? 0 : 1;
+                L3.stop = (beta > 0.0f && isfinite(beta)) ? 0 : 1;
+                L3.beta = beta;
+                if (!L3.stop) {
+                    L3.inv = div_rn(1.0f, beta);
+                    L3.g[0] = beta;
+                    L3.sigma = C.P.scale_cast ? pow2_scale_f(mul_rn(r3[1], L3.inv)) : 1.0f;
+                    L3.inv_sigma = div_rn(1.0f, L3.sigma);
+                }
+            }
+            __syncthreads();
+        } else {
+            team_sync();
+        }
+    }
+    // out = sum_k y_k Z[k]
+    const int k = L.stop && L.kdim == 0 ? 0 : L.kdim;
+    const bool nan_out = L.nonfinite && L.kdim == 0;
+    for (int i = tm.tid; i < n; i += tm.nthr) {
+        float s = 0.0f;
+        for (int l = 0; l < k; ++l) s = fma_rn(L.y[l], ldcg(Z + (size_t)l * ld + i), s);
+        if (nan_out) s = NAN;
+        if (LEVEL == 2) out64[i] = mul_rn(__ldg(S.dsc + i), (double)s);
+        else out32[i] = s;
+    }
+}
+
+// ------------------------------------------------------- one instance solve
+__device__ void solve_instance(const Team &tm, Shared &sh, const Sys &S, const Inst &I, const BP &P, Out &o) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int n = S.n, ld = I.ld, m1 = P.m1;
+    Ctx2 C{tm, sh, S, I, P, o};
+    double *H = I.H1, *cs = H + (m1 + 1) * m1, *sn = cs + m1, *g = sn + m1, *y = g + m1 + 1;
+    const int ldh = m1 + 1;
+    o = Out{F3R_NOT_CONVERGED, 0, 0, 0.0, 0, 0};
+    // ||b||
+    double accb[1] = {0.0};
+    for (int i = tm.tid; i < n; i += tm.nthr) accb[0] = fma_rn(I.b[i], I.b[i], accb[0]);
+    double nbv[1];
+    team_reduce<double>(tm, sh, accb, 1, nbv);
+    const double nb = sqrt_rn(nbv[0]);
+    if (threadIdx.x == 0) {
+        sh.c_ntr = 1;
+        sh.omega[0] = sh.omega[1] = (P.omega_fixed > 0.0f) ? P.omega_fixed : 1.0f;
+    }
+    __syncthreads();
+    if (!(nb > 0.0)) {
+        for (int i = tm.tid; i < n; i += tm.nthr) I.x[i] = 0.0;
+        o.status = isfinite(nb) ? F3R_OK : F3R_ERR_NONFINITE;
+        return;
+    }
+    int total = 0, cycles = 0;
+    for (;;) {
+        // r = b - A x
+        double ar[1] = {0.0};
+        for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
+            const double ax = row_sum<double>(S, S.a64, s, tm.lane, [&](int c) { return ldcg(I.x + c); });
+            const int i = s * kSlice + tm.lane;
+            if (i < n) {
+                const double ri = sub_rn(I.b[i], ax);
+                I.w1[i] = ri;
+                ar[0] = fma_rn(ri, ri, ar[0]);
+            }
+        }
+        double bb[1];
+        team_reduce<double>(tm, sh, ar, 1, bb);
+        const double beta = sqrt_rn(bb[0]);
+        const double rel = div_rn(beta, nb);
+        o.rel = rel;
+        if (!isfinite(beta)) {
+            o.status = F3R_ERR_NONFINITE;
+            break;
+        }
+        if (rel < P.tol) {
+            o.status = F3R_OK;
+            break;
+        }
+        if (total >= P.max_outer) break;
+        ++cycles;
+        const double inv0 = div_rn(1.0, beta);
+        if (tm.rank == 0 && threadIdx.x == 0) g[0] = beta;
+        // V1[0] = r / beta, F2 input (fp32 of D^-1/2 V1[0]) in V2[0]
+        double inv = inv0;
+        int kdim = 0;
+        bool nonfinite = false;
+        for (int j = 0; j < m1; ++j) {
+            float a2[2] = {0.0f, 0.0f};
+            for (int i = tm.tid; i < n; i += tm.nthr) {
+                const double v = mul_rn(ldcg(j == 0 ? I.w1 + i : I.w1 + i), inv);
+                I.V1[(size_t)j * ld + i] = v;
+                const float c = __double2float_rn(mul_rn(__ldg(S.dsc + i), v));
+                I.V2[i] = c;
+                a2[0] = fma_rn(c, c, a2[0]);
+            }
+            float r2[1];
+            team_reduce<float>(tm, sh, a2, 1, r2);
+            if (threadIdx.x == 0) {
+                LS &L2 = sh.ls2;
+                const float b2 = sqrt_rn(r2[0]);
+                L2.kdim = 0;
+                L2.nonfinite = isfinite(b2) ? 0 : 1;
+                L2.stop = (b2 > 0.0f && isfinite(b2)) ? 0 : 1;
+                L2.beta = b2;
+                if (!L2.stop) {
+                    L2.inv = div_rn(1.0f, b2);
+                    L2.g[0] = b2;
+                }
+            }
+            __syncthreads();
+            // Z1[j] = D^-1/2 F2(D^-1/2 V1[j])
+            double *zj = I.Z1 + (size_t)j * ld;
+            inner_level<2>(C, I.V2, I.Z2, I.w2, sh.ls2, P.m2, nullptr, zj);
+            team_sync();
+            // w = A Z1[j]; CGS2 against V1[0..j] in chunks of kRedMax
+            for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
+                const double yv = row_sum<double>(S, S.a64, s, tm.lane, [&](int c) { return ldcg(zj + c); });
+                const int i = s * kSlice + tm.lane;
+                if (i < n) I.w1[i] = yv;
+            }
+            team_sync();
+            double hsum[kMaxOuterM + 1];
+            for (int p = 0; p < P.cgs_passes; ++p) {
+                double h[kMaxOuterM + 1];
+                for (int l0 = 0; l0 <= j; l0 += kRedMax) {
+                    const int cnt = min(kRedMax, j + 1 - l0);
+                    double acc[kRedMax];
+                    for (int l = 0; l < kRedMax; ++l) acc[l] = 0.0;
+                    for (int i = tm.tid; i < n; i += tm.nthr) {
+                        const double wi = ldcg(I.w1 + i);
+                        for (int l = 0; l < cnt; ++l) acc[l] = fma_rn(ldcg(I.V1 + (size_t)(l0 + l) * ld + i), wi, acc[l]);
+                    }
+                    team_reduce<double>(tm, sh, acc, cnt, h + l0);
+                }
+                for (int i = tm.tid; i < n; i += tm.nthr) {
+                    double wi = ldcg(I.w1 + i);
+                    for (int l = 0; l <= j; ++l) wi = fma_rn(-h[l], ldcg(I.V1 + (size_t)l * ld + i), wi);
+                    I.w1[i] = wi;
+                }
+                for (int l = 0; l <= j; ++l) hsum[l] = (p == 0) ? h[l] : add_rn(hsum[l], h[l]);
+                team_sync();
+            }
+            double an[1] = {0.0};
+            for (int i = tm.tid; i < n; i += tm.nthr) {
+                const double wi = ldcg(I.w1 + i);
+                an[0] = fma_rn(wi, wi, an[0]);
+            }
+            double rn[1];
+            team_reduce<double>(tm, sh, an, 1, rn);
+            const double hn = sqrt_rn(rn[0]);
+            ++total;
+            // outer Givens step (rank 0 owns H1), decisions broadcast
+            if (tm.rank == 0 && threadIdx.x == 0) {
+                bool finite = isfinite(hn);
+                for (int l = 0; l <= j; ++l) finite = finite && isfinite(hsum[l]);
+                bool ok = finite;
+                if (ok) {
+                    for (int l = 0; l <= j; ++l) H[l + ldh * j] = hsum[l];
+                    H[j + 1 + ldh * j] = hn;
+                    for (int l = 0; l < j; ++l) {
+                        const double t = add_rn(mul_rn(cs[l], H[l + ldh * j]), mul_rn(sn[l], H[l + 1 + ldh * j]));
+                        H[l + 1 + ldh * j] = add_rn(mul_rn(-sn[l], H[l + ldh * j]), mul_rn(cs[l], H[l + 1 + ldh * j]));
+                        H[l + ldh * j] = t;
+                    }
+                    const double a = H[j + ldh * j], b = H[j + 1 + ldh * j];
+                    const double rho = sqrt_rn(add_rn(mul_rn(a, a), mul_rn(b, b)));
+                    ok = rho > 0.0 && isfinite(rho);
+                    if (ok) {
+                        cs[j] = div_rn(a, rho);
+                        sn[j] = div_rn(b, rho);
+                        H[j + ldh * j] = rho;
+                        H[j + 1 + ldh * j] = 0.0;
+                        g[j + 1] = mul_rn(-sn[j], g[j]);
+                        g[j] = mul_rn(cs[j], g[j]);
+                    }
+                }
+                sh.o_nonfinite = finite ? 0 : 1;
+                sh.o_kdim = ok ? j + 1 : j;
+                sh.o_stop = (!ok || !(hn > 0.0)) ? 1 : 0;
+                sh.o_inv = (ok && hn > 0.0) ? div_rn(1.0, hn) : 0.0;
+                sh.o_est = div_rn(fabs(g[sh.o_kdim]), nb);
+            }
+            team_sync();
+            const Shared *s0 = cl.map_shared_rank(&sh, 0);
+            const int o_kdim = s0->o_kdim, o_stop = s0->o_stop, o_nf = s0->o_nonfinite;
+            const double o_est = s0->o_est, o_inv = s0->o_inv;
+            team_sync();
+            kdim = o_kdim;
+            if (o_nf) {
+                nonfinite = true;
+                break;
+            }
+            if (o_stop || o_est < P.tol || total >= P.max_outer) break;
+            inv = o_inv;
+            // V1[j+1] = w / ||w|| happens at the top of the next iteration (from w1)
+        }
+        // y = R^-1 g, x += Z1 y
+        if (tm.rank == 0 && threadIdx.x == 0) {
+            for (int r = kdim - 1; r >= 0; --r) {
+                double s = g[r];
+                for (int l = r + 1; l < kdim; ++l) s = fma_rn(-H[r + ldh * l], y[l], s);
+                y[r] = div_rn(s, H[r + ldh * r]);
+            }
+        }
+        team_sync();
+        for (int i = tm.tid; i < n; i += tm.nthr) {
+            double s = 0.0;
+            for (int l = 0; l < kdim; ++l) s = fma_rn(ldcg(y + l), ldcg(I.Z1 + (size_t)l * ld + i), s);
+            I.x[i] = add_rn(ldcg(I.x + i), s);
+        }
+        team_sync();
+        if (nonfinite) {
+            o.status = F3R_ERR_NONFINITE;
+            break;
+        }
+    }
+    o.outer_iters = total;
+    o.restarts = cycles > 0 ? cycles - 1 : 0;
+}
+
+__global__ void __launch_bounds__(kBT) k_batch(const Sys *sys, const Inst *inst, const int *order, int ninst, BP P,
+                                               int *queue, Out *outs) {
+    __shared__ Shared sh;
+    cg::cluster_group cl = cg::this_cluster();
+    Team tm;
+    tm.rank = cl.block_rank();
+    tm.size = cl.num_blocks();
+    tm.tid = (int)tm.rank * blockDim.x + threadIdx.x;
+    tm.nthr = (int)tm.size * blockDim.x;
+    tm.wid = tm.tid >> 5;
+    tm.nwarps = tm.nthr >> 5;
+    tm.lane = threadIdx.x & 31;
+    for (;;) {
+        if (tm.rank == 0 && threadIdx.x == 0) sh.inst = atomicAdd(queue, 1);
+        team_sync();
+        const int q = cl.map_shared_rank(&sh, 0)->inst;
+        team_sync();
+        if (q >= ninst) break;
+        const int k = order[q];
+        const Inst I = inst[k];
+        const Sys S = sys[I.sys];
+        Out o;
+        solve_instance(tm, sh, S, I, P, o);
+        if (tm.rank == 0 && threadIdx.x == 0) outs[k] = o;
+        team_sync();
+    }
+}
+
+}  // namespace bt
+}  // namespace f3r
+
+using namespace f3r;
+
+struct f3r_batch {
+    std::vector<Ctx *> sys;   // matrix of each system (set-up arrays only)
+    std::vector<int> nrhs;
+    std::vector<int> inst_sys, inst_rhs;
+    bt::BP P{};
+    f3r_params prm{};
+    bt::Sys *d_sys = nullptr;
+    bt::Inst *d_inst = nullptr;
+    int *d_order = nullptr, *d_queue = nullptr;
+    bt::Out *d_out = nullptr;
+    std::vector<bt::Inst> h_inst;
+    std::vector<void *> allocs;
+    int cluster = 8, grid = 0;
+    long long bytes = 0;
+    cudaStream_t cs = nullptr;
+};
+
+namespace {
+void *balloc(f3r_batch *b, size_t bytes) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+    b->allocs.push_back(p);
+    b->bytes += (long long)bytes;
+    return p;
+}
+}  // namespace
+
+extern "C" {
+
+f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *desc, const f3r_params *params,
+                             void *stream) {
+    if (!out || nsys <= 0 || !desc) return F3R_ERR_ARG;
+    *out = nullptr;
+    f3r_params prm;
+    if (params) prm = *params;
+    else f3r_default_params(&prm);
+    // the batched path runs the default F3R precision schedule
+    if (prm.nlevels != 3 || prm.rich_m != 2 || prm.a_prec[1] != F3R_F32 || prm.a_prec[2] != F3R_F16 ||
+        prm.v_prec[1] != F3R_F32 || prm.v_prec[2] != F3R_F32 || prm.rich_a_prec != F3R_F16 ||
+        prm.rich_v_prec != F3R_F16 || prm.m_prec != F3R_F16 || prm.row_scale)
+        return F3R_ERR_UNSUPPORTED;
+    if (prm.m[0] < 1 || prm.m[0] > kMaxOuterM || prm.m[1] < 1 || prm.m[1] > kMaxInnerM || prm.m[2] < 1 ||
+        prm.m[2] > kMaxInnerM || prm.c < 1 || prm.max_outer < 1 || (prm.cgs_passes != 1 && prm.cgs_passes != 2))
+        return F3R_ERR_ARG;
+    f3r_batch *b = new (std::nothrow) f3r_batch;
+    if (!b) return F3R_ERR_NOMEM;
+    b->prm = prm;
+    auto fail = [&](f3r_status e) {
+        f3r_destroy_batched(b);
+        return e;
+    };
+    if (cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) != cudaSuccess) return fail(F3R_ERR_CUDA);
+    cudaStream_t s = b->cs;
+    cudaEvent_t ev;
+    cudaEventCreate(&ev);
+    cudaEventRecord(ev, (cudaStream_t)stream);
+    cudaStreamWaitEvent(s, ev, 0);
+    cudaEventDestroy(ev);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<bt::Sys> hs(nsys);
+    for (int k = 0; k < nsys; ++k) {
+        const f3r_system_desc &d = desc[k];
+        if (d.n <= 0 || d.nrhs < 1 || !d.rowptr || !d.colidx || !d.val) return fail(F3R_ERR_ARG);
+        Ctx *c = new (std::nothrow) Ctx;
+        if (!c) return fail(F3R_ERR_NOMEM);
+        b->sys.push_back(c);
+        c->dev = dev;
+        c->nsm = nsm;
+        c->prm = prm;
+        c->n = d.n;
+        c->nnz = d.nnz;
+        c->ld = (int)(((long long)d.n + 255) / 256 * 256);
+        // upload the CSR arrays (host or device) and build the copies of A
+        void *tmp[3] = {nullptr, nullptr, nullptr};
+        const size_t sz[3] = {sizeof(int) * ((size_t)d.n + 1), sizeof(int) * (size_t)d.nnz, sizeof(double) * (size_t)d.nnz};
+        const void *src[3] = {d.rowptr, d.colidx, d.val};
+        const void *dp[3];
+        for (int q = 0; q < 3; ++q) {
+            cudaPointerAttributes a;
+            const bool on_dev = cudaPointerGetAttributes(&a, src[q]) == cudaSuccess &&
+                                (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+            cudaGetLastError();
+            if (on_dev) {
+                dp[q] = src[q];
+            } else {
+                if (cudaMalloc(&tmp[q], sz[q] ? sz[q] : 16) != cudaSuccess) return fail(F3R_ERR_NOMEM);
+                cudaMemcpyAsync(tmp[q], src[q], sz[q], cudaMemcpyHostToDevice, s);
+                dp[q] = tmp[q];
+            }
+        }
+        f3r_status st = build_matrix(*c, (const int *)dp[0], (const int *)dp[1], (const double *)dp[2], s);
+        for (void *p : tmp)
+            if (p) cudaFree(p);
+        if (st != F3R_OK) return fail(st);
+        hs[k] = bt::Sys{c->n, c->nslices, c->sptr, c->col, c->a64, c->a32, c->a16, c->dsc, (const h16 *)c->mvec};
+        for (int r = 0; r < d.nrhs; ++r) {
+            b->inst_sys.push_back(k);
+            b->inst_rhs.push_back(r);
+        }
+        b->nrhs.push_back(d.nrhs);
+    }
+    // per-instance workspace
+    const int m1 = prm.m[0], m2 = prm.m[1], m3 = prm.m[2];
+    const int ninst = (int)b->inst_sys.size();
+    b->h_inst.resize(ninst);
+    for (int q = 0; q < ninst; ++q) {
+        const Ctx &c = *b->sys[b->inst_sys[q]];
+        const size_t ld = c.ld;
+        bt::Inst &I = b->h_inst[q];
+        I.sys = b->inst_sys[q];
+        I.ld = (int)ld;
+        I.b = nullptr;
+        I.x = nullptr;
+        I.V1 = (double *)balloc(b, sizeof(double) * ld * (m1 + 1));
+        I.Z1 = (double *)balloc(b, sizeof(double) * ld * m1);
+        I.w1 = (double *)balloc(b, sizeof(double) * ld);
+        I.H1 = (double *)balloc(b, sizeof(double) * ((m1 + 1) * m1 + 4 * m1 + 2));
+        I.V2 = (float *)balloc(b, sizeof(float) * ld * (m2 + 1));
+        I.Z2 = (float *)balloc(b, sizeof(float) * ld * m2);
+        I.w2 = (float *)balloc(b, sizeof(float) * ld);
+        I.V3 = (float *)balloc(b, sizeof(float) * ld * (m3 + 1));
+        I.Z3 = (float *)balloc(b, sizeof(float) * ld * m3);
+        I.w3 = (float *)balloc(b, sizeof(float) * ld);
+        I.rin = (h16 *)balloc(b, sizeof(h16) * ld);
+        I.rz = (h16 *)balloc(b, sizeof(h16) * ld);
+        I.rr = (h16 *)balloc(b, sizeof(h16) * ld);
+        if (!I.V1 || !I.Z1 || !I.w1 || !I.H1 || !I.V2 || !I.Z2 || !I.w2 || !I.V3 || !I.Z3 || !I.w3 || !I.rin ||
+            !I.rz || !I.rr)
+            return fail(F3R_ERR_NOMEM);
+    }
+    b->d_sys = (bt::Sys *)balloc(b, sizeof(bt::Sys) * nsys);
+    b->d_inst = (bt::Inst *)balloc(b, sizeof(bt::Inst) * ninst);
+    b->d_order = (int *)balloc(b, sizeof(int) * ninst);
+    b->d_queue = (int *)balloc(b, sizeof(int) * 4);
+    b->d_out = (bt::Out *)balloc(b, sizeof(bt::Out) * ninst);
+    if (!b->d_sys || !b->d_inst || !b->d_order || !b->d_queue || !b->d_out) return fail(F3R_ERR_NOMEM);
+    cudaMemcpyAsync(b->d_sys, hs.data(), sizeof(bt::Sys) * nsys, cudaMemcpyHostToDevice, s);
+    // largest instances first
+    std::vector<int> order(ninst);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return b->sys[b->inst_sys[a]]->nnz > b->sys[b->inst_sys[c]]->nnz;
+    });
+    cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s);
+    b->P = bt::BP{m1, m2, m3, prm.c, prm.max_outer, prm.cgs_passes, prm.scale_cast, prm.tol, (float)prm.omega_fixed};
+    b->cluster = 8;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(F3R_ERR_CUDA);
+    *out = b;
+    return F3R_OK;
+}
+
+f3r_status f3r_batched_set_cluster(f3r_batch *b, int cluster_size) {
+    if (!b || cluster_size < 1 || cluster_size > bt::kMaxCluster || (cluster_size & (cluster_size - 1))) return F3R_ERR_ARG;
+    b->cluster = cluster_size;
+    return F3R_OK;
+}
+
+f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const *X, f3r_batch_result *res,
+                             void *stream) {
+    if (!b || !B || !X) return F3R_ERR_ARG;
+    cudaStream_t s = b->cs;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, (cudaStream_t)stream);
+    cudaStreamWaitEvent(s, e0, 0);
+    const int ninst = (int)b->h_inst.size();
+    for (int q = 0; q < ninst; ++q) {
+        b->h_inst[q].b = B[q];
+        b->h_inst[q].x = X[q];
+    }
+    cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(bt::Inst) * ninst, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(b->d_queue, 0, sizeof(int) * 4, s);
+    cudaLaunchConfig_t cfg = {};
+    const int cl = b->cluster;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(bt::kBT, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    cfg.gridDim = dim3(cl, 1, 1);
+    if (cudaOccupancyMaxActiveClusters(&ncl, (void *)bt::k_batch, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        ncl = 1;
+    }
+    ncl = std::min(ncl, ninst);
+    cfg.gridDim = dim3(ncl * cl, 1, 1);
+    b->grid = ncl * cl;
+    cudaEventRecord(e0, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, bt::k_batch, (const bt::Sys *)b->d_sys, (const bt::Inst *)b->d_inst,
+                                       (const int *)b->d_order, ninst, b->P, b->d_queue, b->d_out);
+    cudaEventRecord(e1, s);
+    if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaGetLastError();
+        return F3R_ERR_CUDA;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    std::vector<bt::Out> ho(ninst);
+    cudaMemcpy(ho.data(), b->d_out, sizeof(bt::Out) * ninst, cudaMemcpyDeviceToHost);
+    f3r_status worst = F3R_OK;
+    for (int q = 0; q < ninst; ++q) {
+        if (ho[q].status != F3R_OK && worst == F3R_OK) worst = (f3r_status)ho[q].status;
+        if (res) {
+            res[q].status = ho[q].status;
+            res[q].outer_iters = ho[q].outer_iters;
+            res[q].restarts = ho[q].restarts;
+            res[q].rel_res_true = ho[q].rel;
+            res[q].m_applies = ho[q].m_applies;
+            res[q].r_calls = ho[q].r_calls;
+            res[q].t_solve_ms = ms;
+            res[q].system = b->inst_sys[q];
+            res[q].rhs = b->inst_rhs[q];
+        }
+    }
+    cudaEventRecord(e1, s);
+    cudaStreamWaitEvent((cudaStream_t)stream, e1, 0);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return worst;
+}
+
+// Autotuner of the batched launch shape: time one outer iteration of the
+// whole batch (from x0 = 0) for every cluster size that fits, keep the
+// fastest.  X is zeroed again on return.
+f3r_status f3r_batched_autotune(f3r_batch *b, const double *const *B, double *const *X, int *chosen, void *stream) {
+    if (!b || !B || !X) return F3R_ERR_ARG;
+    const int saved_outer = b->P.max_outer;
+    const int cand[4] = {1, 2, 4, 8};
+    float best = 3.0e38f;
+    int best_c = b->cluster;
+    const int ninst = (int)b->h_inst.size();
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int ci = 0; ci < 4; ++ci) {
+        b->cluster = cand[ci];
+        b->P.max_outer = 1;
+        for (int q = 0; q < ninst; ++q)
+            cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
+        cudaEventRecord(e0, b->cs);
+        f3r_status st = f3r_solve_batched(b, B, X, nullptr, stream);
+        cudaEventRecord(e1, b->cs);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if ((st == F3R_OK || st == F3R_NOT_CONVERGED) && ms < best) {
+            best = ms;
+            best_c = cand[ci];
+        }
+    }
+    b->P.max_outer = saved_outer;
+    b->cluster = best_c;
+    for (int q = 0; q < ninst; ++q) cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
+    cudaStreamSynchronize(b->cs);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (chosen) *chosen = best_c;
+    return F3R_OK;
+}
+
+int f3r_batched_instances(const f3r_batch *b) { return b ? (int)b->h_inst.size() : 0; }
+
+int64_t f3r_batched_device_bytes(const f3r_batch *b) {
+    if (!b) return 0;
+    long long t = b->bytes;
+    for (Ctx *c : b->sys) t += c->bytes;
+    return t;
+}
+
+void f3r_destroy_batched(f3r_batch *b) {
+    if (!b) return;
+    for (Ctx *c : b->sys) {
+        for (void *p : c->allocs) cudaFree(p);
+        delete c;
+    }
+    for (void *p : b->allocs) cudaFree(p);
+    if (b->cs) cudaStreamDestroy(b->cs);
+    delete b;
+}
+
+}  // extern "C"

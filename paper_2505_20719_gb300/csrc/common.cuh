@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "f3r.h"
 
 namespace f3r {
@@ -106,9 +108,10 @@ template <class T> struct GridRed {
 // and block shape, so results are reproducible run to run.
 template <class T, int ND, class Fin>
 __device__ __forceinline__ void grid_reduce(T (&acc)[ND], int nd, bool with_max, GridRed<T> gr, Fin fin) {
-    __shared__ T sm[ND][kWarps];
+    __shared__ T sm[ND][32];
     __shared__ bool am_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     const int ntot = nd + (with_max ? 1 : 0);
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
@@ -121,7 +124,7 @@ __device__ __forceinline__ void grid_reduce(T (&acc)[ND], int nd, bool with_max,
     if (threadIdx.x < ntot) {
         const int d = threadIdx.x;
         T s = sm[d][0];
-        for (int w = 1; w < kWarps; ++w) s = (with_max && d == nd) ? fmax(s, sm[d][w]) : add_rn(s, sm[d][w]);
+        for (int w = 1; w < nwarps; ++w) s = (with_max && d == nd) ? fmax(s, sm[d][w]) : add_rn(s, sm[d][w]);
         gr.partials[(size_t)blockIdx.x * gr.stride + d] = s;
     }
     __threadfence();
@@ -160,7 +163,7 @@ __device__ __forceinline__ void grid_reduce(T (&acc)[ND], int nd, bool with_max,
         for (int d = 0; d < ND; ++d) {
             if (d < ntot) {
                 T s = sm[d][0];
-                for (int w = 1; w < kWarps; ++w) s = (with_max && d == nd) ? fmax(s, sm[d][w]) : add_rn(s, sm[d][w]);
+                for (int w = 1; w < nwarps; ++w) s = (with_max && d == nd) ? fmax(s, sm[d][w]) : add_rn(s, sm[d][w]);
                 res[d] = s;
             } else {
                 res[d] = (T)0;
@@ -201,6 +204,35 @@ __device__ __forceinline__ TC sell_row(const Sell &S, const TA *__restrict__ val
 }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Programmatic dependent launch: a kernel first lets the next kernel in the
+// stream start launching (its blocks fill SMs as this grid drains), then waits
+// until every prerequisite grid has completed and its writes are visible.
+// Both are no-ops for a launch without the programmatic attribute.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// programmatic dependent launch, on when F3R_PDL=1 is set in the environment
+bool pdl_enabled();
+
+// launch with the programmatic-stream-serialization attribute
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 }  // namespace f3r
 

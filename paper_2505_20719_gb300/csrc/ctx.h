@@ -10,6 +10,8 @@
 
 namespace f3r {
 
+struct LearnedState;
+
 struct LevelHost {
     int m = 0, a_prec = 0, v_prec = 0, child = 2;
     void *V = nullptr, *Z = nullptr, *w = nullptr, *scal = nullptr;
@@ -75,7 +77,7 @@ struct Ctx {
     // reductions and flags
     void *partials = nullptr;
     unsigned *ticket = nullptr;
-    int G = 1, Gs = 1, G1 = 1;
+    int G = 1, Gs = 1, G1 = 1, Gv = 1;  // grids: elementwise, SpMV, outer CGS, streaming vector kernels
     int *flags = nullptr;       // 4 ints per level
     int *err = nullptr;         // device error word (bounded waits that gave up)
     bool staged = true;         // stage SELL slices through shared memory
@@ -97,6 +99,7 @@ struct Ctx {
     size_t prec_used = 0;
     double prof_ms[kProfSlots] = {};
     long long prof_cnt[kProfSlots] = {};
+    LearnedState *learned = nullptr;  // learned preconditioner (precond = F3R_PC_LEARNED)
 };
 
 inline void prof_begin(Ctx &c, int kind, int level, cudaStream_t s) {
@@ -151,6 +154,17 @@ f3r_status launch_spmv(Ctx &c, int p, int vp, const void *x, void *y, cudaStream
 // launch_rich.cu
 void launch_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s);
 void launch_rich_prep(Ctx &c, const void *x, cudaStream_t s);
+
+// learned.cu
+f3r_status learned_enable(Ctx &c, const float *theta, bool train);
+void learned_forward(Ctx &c, const float *r, float *z, bool train, cudaStream_t s);
+f3r_status learned_loss_grad(Ctx &c, const float *R, const float *E, int P, cudaStream_t s);
+void learned_adam(Ctx &c, float lr, cudaStream_t s);
+void learned_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s);
+void learned_free(Ctx &c);
+float *learned_theta(Ctx &c);
+float *learned_grad(Ctx &c);
+float *learned_loss(Ctx &c);
 
 // sizes
 int prec_bytes(int p);

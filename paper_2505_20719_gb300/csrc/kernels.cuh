@@ -118,6 +118,7 @@ template <class TA, class T>
 __global__ void __launch_bounds__(kBlock) k_spmv_dots(Sell S, const TA *__restrict__ val,
                                                       const float *__restrict__ rs, LevelDev<T> L, int j,
                                                       GridRed<T> gr) {
+    pdl_enter();
     if (stopped(L.flags, L.depth)) return;
     const T *__restrict__ x = L.Z + (size_t)j * L.ld;
     T acc[kMaxDots];
@@ -143,10 +144,21 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dots(Sell S, const TA *__restri
     });
 }
 
+constexpr int kVecBlock = 512;  // threads per block of the streaming vector kernels
+constexpr int kUnroll = 1;       // 16-byte packs in flight per thread and vector
+
+// Grid-stride walk over 16-byte packs, kUnroll packs per thread per step:
+// f(q, valid) is called for packs q = base + tid + u * nth (coalesced per u).
+template <class F> __device__ __forceinline__ void for_packs(int npacks, F f) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int base = 0; base < npacks; base += nth * kUnroll) f(base + tid, nth);
+}
+
 // w -= V[0..j] h (fma in l order), then hB = V[0..j]^T w.  Streams 16-byte
 // packs; MAXD bounds j + 1 so the register footprint follows the level size.
 template <class T, int MAXD>
-__global__ void __launch_bounds__(kBlock) k_cgs_pass(LevelDev<T> L, int j, GridRed<T> gr) {
+__global__ void __launch_bounds__(kVecBlock) k_cgs_pass(LevelDev<T> L, int j, GridRed<T> gr) {
+    pdl_enter();
     if (stopped(L.flags, L.depth)) return;
     constexpr int N = PackN<T>::N;
     __shared__ T hs[MAXD];
@@ -155,30 +167,43 @@ __global__ void __launch_bounds__(kBlock) k_cgs_pass(LevelDev<T> L, int j, GridR
     T acc[MAXD];
 #pragma unroll
     for (int l = 0; l < MAXD; ++l) acc[l] = (T)0;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const int nq = L.n / N;
     T *__restrict__ w = L.w;
     const T *__restrict__ V = L.V;
-    for (int q = tid; q < nq; q += nth) {
-        Pack<T, N> wv = ldp<T, N>(w + (size_t)q * N);
-        Pack<T, N> v[MAXD];
+    for_packs(nq, [&](int q0, int nth) {
+        Pack<T, N> wv[kUnroll];
+        Pack<T, N> v[kUnroll][MAXD];
 #pragma unroll
-        for (int l = 0; l < MAXD; ++l)
-            if (l <= j) v[l] = ldp<T, N>(V + (size_t)l * L.ld + (size_t)q * N);
+        for (int u = 0; u < kUnroll; ++u) {
+            const int q = q0 + u * nth;
+            if (q < nq) {
+                wv[u] = ldp<T, N>(w + (size_t)q * N);
 #pragma unroll
-        for (int l = 0; l < MAXD; ++l)
-            if (l <= j) {
-#pragma unroll
-                for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-hs[l], v[l].v[e], wv.v[e]);
+                for (int l = 0; l < MAXD; ++l)
+                    if (l <= j) v[u][l] = ldp<T, N>(V + (size_t)l * L.ld + (size_t)q * N);
             }
-        stp<T, N>(w + (size_t)q * N, wv);
+        }
 #pragma unroll
-        for (int l = 0; l < MAXD; ++l)
-            if (l <= j) {
+        for (int u = 0; u < kUnroll; ++u) {
+            const int q = q0 + u * nth;
+            if (q < nq) {
 #pragma unroll
-                for (int e = 0; e < N; ++e) acc[l] = fma_rn(v[l].v[e], wv.v[e], acc[l]);
+                for (int l = 0; l < MAXD; ++l)
+                    if (l <= j) {
+#pragma unroll
+                        for (int e = 0; e < N; ++e) wv[u].v[e] = fma_rn(-hs[l], v[u][l].v[e], wv[u].v[e]);
+                    }
+                stp<T, N>(w + (size_t)q * N, wv[u]);
+#pragma unroll
+                for (int l = 0; l < MAXD; ++l)
+                    if (l <= j) {
+#pragma unroll
+                        for (int e = 0; e < N; ++e) acc[l] = fma_rn(v[u][l].v[e], wv[u].v[e], acc[l]);
+                    }
             }
-    }
+        }
+    });
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     for (int i = nq * N + tid; i < L.n; i += nth) {
         T wi = w[i];
         T v[MAXD];
@@ -202,8 +227,9 @@ __global__ void __launch_bounds__(kBlock) k_cgs_pass(LevelDev<T> L, int j, GridR
 // w -= V[0..j] h_last; ||w||^2 and max|w|; Givens step with column hA (+ hB);
 // the scale of the child's 16-bit cast of V[j+1] from max|w| / ||w||.
 template <class T, int MAXD>
-__global__ void __launch_bounds__(kBlock) k_cgs_final(LevelDev<T> L, int j, int passes, int last_iter,
-                                                      int want_sigma, GridRed<T> gr) {
+__global__ void __launch_bounds__(kVecBlock) k_cgs_final(LevelDev<T> L, int j, int passes, int last_iter,
+                                                         int want_sigma, GridRed<T> gr) {
+    pdl_enter();
     if (stopped(L.flags, L.depth)) return;
     constexpr int N = PackN<T>::N;
     __shared__ T hs[MAXD];
@@ -211,29 +237,42 @@ __global__ void __launch_bounds__(kBlock) k_cgs_final(LevelDev<T> L, int j, int 
     if (threadIdx.x <= j) hs[threadIdx.x] = hl[threadIdx.x];
     __syncthreads();
     T acc[2] = {(T)0, (T)0};
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const int nq = L.n / N;
     T *__restrict__ w = L.w;
     const T *__restrict__ V = L.V;
-    for (int q = tid; q < nq; q += nth) {
-        Pack<T, N> wv = ldp<T, N>(w + (size_t)q * N);
-        Pack<T, N> v[MAXD];
+    for_packs(nq, [&](int q0, int nth) {
+        Pack<T, N> wv[kUnroll];
+        Pack<T, N> v[kUnroll][MAXD];
 #pragma unroll
-        for (int l = 0; l < MAXD; ++l)
-            if (l <= j) v[l] = ldp<T, N>(V + (size_t)l * L.ld + (size_t)q * N);
+        for (int u = 0; u < kUnroll; ++u) {
+            const int q = q0 + u * nth;
+            if (q < nq) {
+                wv[u] = ldp<T, N>(w + (size_t)q * N);
 #pragma unroll
-        for (int l = 0; l < MAXD; ++l)
-            if (l <= j) {
-#pragma unroll
-                for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-hs[l], v[l].v[e], wv.v[e]);
+                for (int l = 0; l < MAXD; ++l)
+                    if (l <= j) v[u][l] = ldp<T, N>(V + (size_t)l * L.ld + (size_t)q * N);
             }
-        stp<T, N>(w + (size_t)q * N, wv);
-#pragma unroll
-        for (int e = 0; e < N; ++e) {
-            acc[0] = fma_rn(wv.v[e], wv.v[e], acc[0]);
-            acc[1] = fmax(acc[1], fabs(wv.v[e]));
         }
-    }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int q = q0 + u * nth;
+            if (q < nq) {
+#pragma unroll
+                for (int l = 0; l < MAXD; ++l)
+                    if (l <= j) {
+#pragma unroll
+                        for (int e = 0; e < N; ++e) wv[u].v[e] = fma_rn(-hs[l], v[u][l].v[e], wv[u].v[e]);
+                    }
+                stp<T, N>(w + (size_t)q * N, wv[u]);
+#pragma unroll
+                for (int e = 0; e < N; ++e) {
+                    acc[0] = fma_rn(wv[u].v[e], wv[u].v[e], acc[0]);
+                    acc[1] = fmax(acc[1], fabs(wv[u].v[e]));
+                }
+            }
+        }
+    });
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     for (int i = nq * N + tid; i < L.n; i += nth) {
         T wi = w[i];
 #pragma unroll
@@ -279,8 +318,9 @@ template <class TC> struct ChildOut {
 // V[dst] = src * inv (inv = 1/||src|| of this level); child input from it.
 // src == V[0] (in place) at a level start, w otherwise.
 template <class T, class TC, int CHILD>
-__global__ void __launch_bounds__(kBlock) k_normalize(LevelDev<T> L, const T *src, int dst, int check_depth,
+__global__ void __launch_bounds__(kVecBlock) k_normalize(LevelDev<T> L, const T *src, int dst, int check_depth,
                                                       ChildOut<TC> co, GridRed<T> gr) {
+    pdl_enter();
     if (stopped(L.flags, check_depth)) return;
     constexpr int N = PackN<T>::N;
     const int jd = L.jptr ? (*L.jptr + dst) : dst;
@@ -298,19 +338,28 @@ __global__ void __launch_bounds__(kBlock) k_normalize(LevelDev<T> L, const T *sr
             acc[1] = fmax(acc[1], fabs(c));
             return std::pair<T, TC>(v, c);
         };
-        for (int q = tid; q < nq; q += nth) {
-            const Pack<T, N> sp = ldp<T, N>(src + (size_t)q * N);
-            Pack<T, N> op;
-            Pack<TC, N> cp;
+        for_packs(nq, [&](int q0, int nthr) {
+            Pack<T, N> sp[kUnroll];
 #pragma unroll
-            for (int e = 0; e < N; ++e) {
-                auto vc = one(q * N + e, sp.v[e]);
-                op.v[e] = vc.first;
-                cp.v[e] = vc.second;
+            for (int u = 0; u < kUnroll; ++u)
+                if (q0 + u * nthr < nq) sp[u] = ldp<T, N>(src + (size_t)(q0 + u * nthr) * N);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int q = q0 + u * nthr;
+                if (q < nq) {
+                    Pack<T, N> op;
+                    Pack<TC, N> cp;
+#pragma unroll
+                    for (int e = 0; e < N; ++e) {
+                        auto vc = one(q * N + e, sp[u].v[e]);
+                        op.v[e] = vc.first;
+                        cp.v[e] = vc.second;
+                    }
+                    stp<T, N>(out + (size_t)q * N, op);
+                    stp<TC, N>(co.x + (size_t)q * N, cp);
+                }
             }
-            stp<T, N>(out + (size_t)q * N, op);
-            stp<TC, N>(co.x + (size_t)q * N, cp);
-        }
+        });
         for (int i = nq * N + tid; i < L.n; i += nth) {
             auto vc = one(i, src[i]);
             out[i] = vc.first;
@@ -341,19 +390,28 @@ __global__ void __launch_bounds__(kBlock) k_normalize(LevelDev<T> L, const T *sr
             if (L.jptr && dst == 1) atomicAdd(const_cast<int *>(L.jptr), 1);  // closes outer iteration j
         });
     } else {
-        for (int q = tid; q < nq; q += nth) {
-            const Pack<T, N> sp = ldp<T, N>(src + (size_t)q * N);
-            Pack<T, N> op;
+        for_packs(nq, [&](int q0, int nthr) {
+            Pack<T, N> sp[kUnroll];
 #pragma unroll
-            for (int e = 0; e < N; ++e) op.v[e] = mul_rn(sp.v[e], inv);
-            stp<T, N>(out + (size_t)q * N, op);
-            if constexpr (CHILD == CHILD_R) {
-                Pack<TC, N> cp;
+            for (int u = 0; u < kUnroll; ++u)
+                if (q0 + u * nthr < nq) sp[u] = ldp<T, N>(src + (size_t)(q0 + u * nthr) * N);
 #pragma unroll
-                for (int e = 0; e < N; ++e) cp.v[e] = Store<TC>::from(mul_rn(sig, op.v[e]));
-                stp<TC, N>(co.x + (size_t)q * N, cp);
+            for (int u = 0; u < kUnroll; ++u) {
+                const int q = q0 + u * nthr;
+                if (q < nq) {
+                    Pack<T, N> op;
+#pragma unroll
+                    for (int e = 0; e < N; ++e) op.v[e] = mul_rn(sp[u].v[e], inv);
+                    stp<T, N>(out + (size_t)q * N, op);
+                    if constexpr (CHILD == CHILD_R) {
+                        Pack<TC, N> cp;
+#pragma unroll
+                        for (int e = 0; e < N; ++e) cp.v[e] = Store<TC>::from(mul_rn(sig, op.v[e]));
+                        stp<TC, N>(co.x + (size_t)q * N, cp);
+                    }
+                }
             }
-        }
+        });
         for (int i = nq * N + tid; i < L.n; i += nth) {
             const T v = mul_rn(src[i], inv);
             out[i] = v;
@@ -378,9 +436,11 @@ __global__ void __launch_bounds__(kBlock) k_normalize(LevelDev<T> L, const T *sr
 // D^-1/2 when returning to level 0.  A level whose input was non-finite
 // returns NaN so that the outer level notices.
 template <class T, class TP>
-__global__ void __launch_bounds__(kBlock) k_combine(LevelDev<T> L, TP *out_base, const int *out_j, int out_ld,
-                                                    const double *dsc) {
+__global__ void __launch_bounds__(kVecBlock) k_combine(LevelDev<T> L, TP *out_base, const int *out_j, int out_ld,
+                                                       const double *dsc) {
+    pdl_enter();
     if (stopped(L.flags, L.depth - 1)) return;
+    constexpr int N = PackN<T>::N;
     const int *fl = L.fl();
     const int k = fl[IF_KDIM];
     const bool nonfinite = fl[IF_NONFINITE] != 0 && k == 0;
@@ -388,11 +448,39 @@ __global__ void __launch_bounds__(kBlock) k_combine(LevelDev<T> L, TP *out_base,
     if (threadIdx.x < k) ys[threadIdx.x] = L.y()[threadIdx.x];
     __syncthreads();
     TP *out = out_base + (out_j ? (size_t)(*out_j) * out_ld : 0);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
+    auto one = [&](int i, T s) { out[i] = dsc ? (TP)mul_rn(dsc[i], (double)s) : (TP)s; };
+    const bool vec = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((sizeof(TP) * N) % 16 == 0 || sizeof(TP) >= sizeof(T));
+    const int nq = vec ? L.n / N : 0;
+    for_packs(nq, [&](int q0, int nthr) {
+        Pack<T, N> sum[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int e = 0; e < N; ++e) sum[u].v[e] = (T)0;
+        for (int l = 0; l < k; ++l) {
+            Pack<T, N> zl[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (q0 + u * nthr < nq) zl[u] = ldp<T, N>(L.Z + (size_t)l * L.ld + (size_t)(q0 + u * nthr) * N);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (q0 + u * nthr < nq)
+#pragma unroll
+                    for (int e = 0; e < N; ++e) sum[u].v[e] = fma_rn(ys[l], zl[u].v[e], sum[u].v[e]);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int q = q0 + u * nthr;
+            if (q < nq)
+#pragma unroll
+                for (int e = 0; e < N; ++e) one(q * N + e, nonfinite ? (T)NAN : sum[u].v[e]);
+        }
+    });
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int i = nq * N + tid; i < L.n; i += nth) {
         T s = (T)0;
         for (int l = 0; l < k; ++l) s = fma_rn(ys[l], L.Z[(size_t)l * L.ld + i], s);
-        if (nonfinite) s = (T)NAN;
-        out[i] = dsc ? (TP)mul_rn(dsc[i], (double)s) : (TP)s;
+        one(i, nonfinite ? (T)NAN : s);
     }
 }
 
@@ -402,6 +490,7 @@ template <class T, class MS>
 __global__ void __launch_bounds__(kBlock) k_apply_M(const MS *__restrict__ mv, const T *__restrict__ v_base,
                                                     const int *in_j, int ld, T *z, int n, const int *flags,
                                                     int check_depth, long long *m_count) {
+    pdl_enter();
     if (stopped(flags, check_depth)) return;
     const T *__restrict__ v = v_base + (in_j ? (size_t)(*in_j) * ld : 0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -456,6 +545,7 @@ __device__ __forceinline__ void block_sum_into(double v, double *dst, double *sc
 static __global__ void __launch_bounds__(kBlock) k_outer_residual(Sell S, const double *__restrict__ a, const double *b,
                                                            const double *x, LevelDev<double> L, GridRed<double> gr,
                                                            int compute_nb) {
+    pdl_enter();
     double acc[2] = {0.0, 0.0};
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -493,6 +583,7 @@ static __global__ void __launch_bounds__(kBlock) k_outer_residual(Sell S, const 
 
 // w = A Z[j] with the original fp64 A (j read on the device)
 static __global__ void __launch_bounds__(kBlock) k_outer_spmv(Sell S, const double *__restrict__ a, LevelDev<double> L) {
+    pdl_enter();
     const int j = *L.jptr;
     const double *__restrict__ x = L.Z + (size_t)j * L.ld;
     const int lane = threadIdx.x & 31;
@@ -510,6 +601,7 @@ static __global__ void __launch_bounds__(kBlock) k_outer_spmv(Sell S, const doub
 template <int MODE>
 __global__ void __launch_bounds__(512) k_outer_cgs(LevelDev<double> L, int passes, double *partials,
                                                    unsigned *ticket) {
+    pdl_enter();
     __shared__ double bs[kMaxOuterM + 2];
     __shared__ double scratch[16];
     __shared__ double hs[kMaxOuterM + 1];
@@ -564,6 +656,7 @@ __global__ void __launch_bounds__(512) k_outer_cgs(LevelDev<double> L, int passe
 
 // y = R^-1 g over the kept columns (outer level, on exit of a cycle)
 static __global__ void k_outer_solve_y(LevelDev<double> L) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int k = L.fl()[IF_KDIM];
     const int ldh = L.m + 1;
@@ -578,6 +671,7 @@ static __global__ void k_outer_solve_y(LevelDev<double> L) {
 
 // x += sum_{k < kdim} y_k Z[k]
 static __global__ void __launch_bounds__(kBlock) k_outer_update_x(LevelDev<double> L, double *x) {
+    pdl_enter();
     __shared__ double ys[kMaxOuterM];
     const int k = L.fl()[IF_KDIM];
     for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = L.y()[l];

@@ -37,6 +37,7 @@ static int want_sigma(const Ctx &c, int d) {
 // ------------------------------------------------------------------ start
 template <class T>
 __global__ void __launch_bounds__(kBlock) k_level_start(const T *x, LevelDev<T> C, int want_sig, GridRed<T> gr) {
+    pdl_enter();
     T acc[2] = {(T)0, (T)0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C.n; i += gridDim.x * blockDim.x) {
         const T v = x[i];
@@ -66,10 +67,10 @@ __global__ void __launch_bounds__(kBlock) k_level_start(const T *x, LevelDev<T> 
 void launch_level_start(Ctx &c, int d, const void *x, cudaStream_t s) {
     prof_begin(c, PK_START, d, s);
     if (c.L[d].v_prec == F3R_F64)
-        k_level_start<double><<<c.G, kBlock, 0, s>>>((const double *)x, levdev<double>(c, d), want_sigma(c, d),
+        launch_pdl(k_level_start<double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)x, levdev<double>(c, d), want_sigma(c, d),
                                                       gred<double>(c, kMaxDots));
     else
-        k_level_start<float><<<c.G, kBlock, 0, s>>>((const float *)x, levdev<float>(c, d), want_sigma(c, d),
+        launch_pdl(k_level_start<float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)x, levdev<float>(c, d), want_sigma(c, d),
                                                      gred<float>(c, kMaxDots));
     prof_end(c, s);
     c.launches++;
@@ -93,7 +94,7 @@ static void norm_go(Ctx &c, int d, bool from_w, int dst, cudaStream_t s) {
     const T *src = from_w ? L.w : L.V;  // at a level start V[0] is normalised in place
     // V[0] of the outer level is addressed through j (= 0 at a cycle start)
     prof_begin(c, PK_NORMALIZE, d, s);
-    k_normalize<T, TC, CHILD><<<c.G, kBlock, 0, s>>>(L, src, dst, d, co, gred<T>(c, kMaxDots));
+    launch_pdl(k_normalize<T, TC, CHILD>, dim3(c.Gv), dim3(kVecBlock), 0, s, L, src, dst, d, co, gred<T>(c, kMaxDots));
     prof_end(c, s);
     c.launches++;
 }
@@ -134,8 +135,8 @@ void launch_normalize(Ctx &c, int d, bool from_w, int dst, cudaStream_t s) {
 template <class K> static int staged_grid(Ctx &c, K kern, int smem, int work_blocks) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, smem);
-    nb = std::max(1, std::min(nb, 4));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStagedThreads, smem);
+    nb = std::max(1, std::min(nb, 8));
     return std::max(1, std::min(c.nsm * nb, work_blocks));
 }
 
@@ -144,7 +145,7 @@ static void spmv_dots_st_go(Ctx &c, int d, int j, const TA *val, const float *rs
                             cudaStream_t s) {
     auto kern = k_spmv_dots_st<TA, T, S, MAXD>;
     const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
-    kern<<<g, kBlock, pl.smem, s>>>(sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots),
+    launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots),
                                     StageCfg{pl.stage_bytes, c.err});
 }
 
@@ -161,7 +162,7 @@ static void spmv_dots_go(Ctx &c, int d, int j, const TA *val, const float *rs, c
         else if (md == 8) spmv_dots_st_go<TA, T, 2, 8>(c, d, j, val, rs, pl, s);
         else spmv_dots_st_go<TA, T, 2, 16>(c, d, j, val, rs, pl, s);
     } else {
-        k_spmv_dots<TA, T><<<c.Gs, kBlock, 0, s>>>(sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots));
+        launch_pdl(k_spmv_dots<TA, T>, dim3(c.Gs), dim3(kBlock), 0, s, sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots));
     }
 }
 
@@ -183,10 +184,10 @@ void launch_spmv_dots(Ctx &c, int d, int j, cudaStream_t s) {
 
 template <class T, int MAXD> static void cgs_go(Ctx &c, int d, int j, bool final_pass, bool last, cudaStream_t s) {
     if (final_pass)
-        k_cgs_final<T, MAXD><<<c.G, kBlock, 0, s>>>(levdev<T>(c, d), j, c.prm.cgs_passes, last ? 1 : 0,
+        launch_pdl(k_cgs_final<T, MAXD>, dim3(c.Gv), dim3(kVecBlock), 0, s, levdev<T>(c, d), j, c.prm.cgs_passes, last ? 1 : 0,
                                                     want_sigma(c, d), gred<T>(c, kMaxDots));
     else
-        k_cgs_pass<T, MAXD><<<c.G, kBlock, 0, s>>>(levdev<T>(c, d), j, gred<T>(c, kMaxDots));
+        launch_pdl(k_cgs_pass<T, MAXD>, dim3(c.Gv), dim3(kVecBlock), 0, s, levdev<T>(c, d), j, gred<T>(c, kMaxDots));
 }
 
 template <class T> static void cgs_dispatch(Ctx &c, int d, int j, bool final_pass, bool last, cudaStream_t s) {
@@ -216,7 +217,7 @@ void launch_cgs_final(Ctx &c, int d, int j, bool last, cudaStream_t s) {
 template <class T, class TP>
 static void comb_go(Ctx &c, int d, const OutSlot &o, cudaStream_t s) {
     prof_begin(c, PK_COMBINE, d, s);
-    k_combine<T, TP><<<c.G, kBlock, 0, s>>>(levdev<T>(c, d), (TP *)o.ptr, nullptr, 0, o.dscale ? c.dsc : nullptr);
+    launch_pdl(k_combine<T, TP>, dim3(c.Gv), dim3(kVecBlock), 0, s, levdev<T>(c, d), (TP *)o.ptr, nullptr, 0, o.dscale ? c.dsc : nullptr);
     prof_end(c, s);
     c.launches++;
 }
@@ -240,17 +241,17 @@ void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, 
     prof_begin(c, PK_M, d, s);
     if (t64) {
         switch (c.prm.m_prec) {
-            case F3R_F64: k_apply_M<double, double><<<c.G, kBlock, 0, s>>>((const double *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            case F3R_F32: k_apply_M<double, float><<<c.G, kBlock, 0, s>>>((const float *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            case F3R_F16: k_apply_M<double, h16><<<c.G, kBlock, 0, s>>>((const h16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            default: k_apply_M<double, b16><<<c.G, kBlock, 0, s>>>((const b16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F64: launch_pdl(k_apply_M<double, double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F32: launch_pdl(k_apply_M<double, float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F16: launch_pdl(k_apply_M<double, h16>, dim3(c.G), dim3(kBlock), 0, s, (const h16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            default: launch_pdl(k_apply_M<double, b16>, dim3(c.G), dim3(kBlock), 0, s, (const b16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
         }
     } else {
         switch (c.prm.m_prec) {
-            case F3R_F32: k_apply_M<float, float><<<c.G, kBlock, 0, s>>>((const float *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            case F3R_F16: k_apply_M<float, h16><<<c.G, kBlock, 0, s>>>((const h16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            case F3R_BF16: k_apply_M<float, b16><<<c.G, kBlock, 0, s>>>((const b16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            default: k_apply_M<float, double><<<c.G, kBlock, 0, s>>>((const double *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F32: launch_pdl(k_apply_M<float, float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F16: launch_pdl(k_apply_M<float, h16>, dim3(c.G), dim3(kBlock), 0, s, (const h16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_BF16: launch_pdl(k_apply_M<float, b16>, dim3(c.G), dim3(kBlock), 0, s, (const b16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            default: launch_pdl(k_apply_M<float, double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
         }
     }
     prof_end(c, s);
@@ -260,7 +261,7 @@ void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, 
 // ------------------------------------------------------------ outer level
 void launch_outer_residual(Ctx &c, const double *b, const double *x, bool compute_nb, cudaStream_t s) {
     prof_begin(c, PK_OUTER_OTHER, 0, s);
-    k_outer_residual<<<c.Gs, kBlock, 0, s>>>(sell_of(c), c.a64, b, x, levdev<double>(c, 0), gred<double>(c, kMaxDots),
+    launch_pdl(k_outer_residual, dim3(c.Gs), dim3(kBlock), 0, s, sell_of(c), c.a64, b, x, levdev<double>(c, 0), gred<double>(c, kMaxDots),
                                               compute_nb ? 1 : 0);
     prof_end(c, s);
     c.launches++;
@@ -268,6 +269,7 @@ void launch_outer_residual(Ctx &c, const double *b, const double *x, bool comput
 
 // w = A z (z = the inner nest's output), Z[j] = z, CGS2, Givens, estimate
 __global__ void __launch_bounds__(kBlock) k_outer_store_z(LevelDev<double> L, const double *z) {
+    pdl_enter();
     const int j = *L.jptr;
     double *dst = L.Z + (size_t)j * L.ld;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) dst[i] = z[i];
@@ -280,27 +282,27 @@ void launch_outer_step(Ctx &c, cudaStream_t s) {
     if (pl.S == 3) {
         auto kern = k_outer_spmv_st<3>;
         const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
-        kern<<<g, kBlock, pl.smem, s>>>(sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err});
+        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err});
         c.launches--;
     } else if (pl.S == 2) {
         auto kern = k_outer_spmv_st<2>;
         const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
-        kern<<<g, kBlock, pl.smem, s>>>(sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err});
+        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err});
         c.launches--;
     } else {
-        k_outer_store_z<<<c.G, kBlock, 0, s>>>(L, (const double *)c.zst);
-        k_outer_spmv<<<c.Gs, kBlock, 0, s>>>(sell_of(c), c.a64, L);
+        launch_pdl(k_outer_store_z, dim3(c.G), dim3(kBlock), 0, s, L, (const double *)c.zst);
+        launch_pdl(k_outer_spmv, dim3(c.Gs), dim3(kBlock), 0, s, sell_of(c), c.a64, L);
     }
     prof_end(c, s);
     double *part = (double *)c.partials;
     prof_begin(c, PK_OUTER_CGS, 0, s);
-    k_outer_cgs<0><<<c.G1, 512, 0, s>>>(L, c.prm.cgs_passes, part, c.ticket);
+    launch_pdl(k_outer_cgs<0>, dim3(c.G1), dim3(512), 0, s, L, c.prm.cgs_passes, part, c.ticket);
     c.launches += 3;
     if (c.prm.cgs_passes == 2) {
-        k_outer_cgs<1><<<c.G1, 512, 0, s>>>(L, c.prm.cgs_passes, part, c.ticket);
+        launch_pdl(k_outer_cgs<1>, dim3(c.G1), dim3(512), 0, s, L, c.prm.cgs_passes, part, c.ticket);
         c.launches++;
     }
-    k_outer_cgs<2><<<c.G1, 512, 0, s>>>(L, c.prm.cgs_passes, part, c.ticket);
+    launch_pdl(k_outer_cgs<2>, dim3(c.G1), dim3(512), 0, s, L, c.prm.cgs_passes, part, c.ticket);
     prof_end(c, s);
     c.launches++;
 }
@@ -308,19 +310,20 @@ void launch_outer_step(Ctx &c, cudaStream_t s) {
 void launch_outer_finish(Ctx &c, double *x, cudaStream_t s) {
     LevelDev<double> L = levdev<double>(c, 0);
     prof_begin(c, PK_OUTER_OTHER, 0, s);
-    k_outer_solve_y<<<1, 32, 0, s>>>(L);
-    k_outer_update_x<<<c.G, kBlock, 0, s>>>(L, x);
+    launch_pdl(k_outer_solve_y, dim3(1), dim3(32), 0, s, L);
+    launch_pdl(k_outer_update_x, dim3(c.G), dim3(kBlock), 0, s, L, x);
     prof_end(c, s);
     c.launches += 2;
 }
 
 __global__ void k_advance(long long *p, long long inc) {
+    pdl_enter();
     if (threadIdx.x == 0 && blockIdx.x == 0) *p += inc;
 }
 
 void launch_advance(Ctx &c, long long inc, cudaStream_t s) {
     prof_begin(c, PK_OUTER_OTHER, 0, s);
-    k_advance<<<1, 32, 0, s>>>(c.c_ntr_base, inc);
+    launch_pdl(k_advance, dim3(1), dim3(32), 0, s, c.c_ntr_base, inc);
     prof_end(c, s);
     c.launches++;
 }
@@ -329,6 +332,7 @@ void launch_advance(Ctx &c, long long inc, cudaStream_t s) {
 template <class TA, class TX, class TY>
 __global__ void __launch_bounds__(kBlock) k_spmv(Sell S, const TA *__restrict__ val, const float *__restrict__ rs,
                                                  const TX *__restrict__ x, TY *y) {
+    pdl_enter();
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -346,14 +350,14 @@ static void spmv_go(Ctx &c, const TA *val, const float *rs, const TX *x, TY *y, 
     const StageCfg cfg{pl.stage_bytes, c.err};
     if (pl.S == 3) {
         auto kern = k_spmv_st<TA, TX, TY, 3>;
-        kern<<<staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices)), kBlock, pl.smem, s>>>(sell_of(c), val, rs,
+        launch_pdl(kern, dim3(staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices))), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs,
                                                                                                 x, y, cfg);
     } else if (pl.S == 2) {
         auto kern = k_spmv_st<TA, TX, TY, 2>;
-        kern<<<staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices)), kBlock, pl.smem, s>>>(sell_of(c), val, rs,
+        launch_pdl(kern, dim3(staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices))), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs,
                                                                                                 x, y, cfg);
     } else {
-        k_spmv<TA, TX, TY><<<c.Gs, kBlock, 0, s>>>(sell_of(c), val, rs, x, y);
+        launch_pdl(k_spmv<TA, TX, TY>, dim3(c.Gs), dim3(kBlock), 0, s, sell_of(c), val, rs, x, y);
     }
 }
 

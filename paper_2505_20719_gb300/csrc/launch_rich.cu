@@ -15,8 +15,8 @@ template <class TC> static RichDev<TC> richdev(Ctx &c) {
 template <class K> static int rich_grid(Ctx &c, K kern, int smem) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBlock, smem);
-    nb = std::max(1, std::min(nb, 4));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStagedThreads, smem);
+    nb = std::max(1, std::min(nb, 8));
     return std::max(1, std::min(c.nsm * nb, ceil_div(c.nslices, kTileSlices)));
 }
 
@@ -37,14 +37,14 @@ static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const 
             const StageCfg cfg{pl.stage_bytes, c.err};
             if (pl.S == 3) {
                 auto kern = k_rich2_st<TA, VS, TC, TP, 3>;
-                kern<<<rich_grid(c, kern, pl.smem), kBlock, pl.smem, s>>>(S, val, rs, v, mv, out, par_misc, R, c.flags,
+                launch_pdl(kern, dim3(rich_grid(c, kern, pl.smem)), dim3(kStagedThreads), pl.smem, s, S, val, rs, v, mv, out, par_misc, R, c.flags,
                                                                           cd, n, cfg);
             } else if (pl.S == 2) {
                 auto kern = k_rich2_st<TA, VS, TC, TP, 2>;
-                kern<<<rich_grid(c, kern, pl.smem), kBlock, pl.smem, s>>>(S, val, rs, v, mv, out, par_misc, R, c.flags,
+                launch_pdl(kern, dim3(rich_grid(c, kern, pl.smem)), dim3(kStagedThreads), pl.smem, s, S, val, rs, v, mv, out, par_misc, R, c.flags,
                                                                           cd, n, cfg);
             } else {
-                k_rich2<TA, VS, TC, TP><<<c.Gs, kBlock, 0, s>>>(S, val, rs, v, mv, out, par_misc, R, c.flags, cd, n);
+                launch_pdl(k_rich2<TA, VS, TC, TP>, dim3(c.Gs), dim3(kBlock), 0, s, S, val, rs, v, mv, out, par_misc, R, c.flags, cd, n);
             }
             prof_end(c, s);
             c.launches++;
@@ -53,7 +53,7 @@ static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const 
                 const bool last = (k == m4 - 1);
                 const VS *zp = (k > 0) ? zb[(k - 1) & 1] : nullptr;
                 prof_begin(c, PK_RICH_STEP, 0, s);
-                k_rich_step<TA, VS, TC, TP><<<c.Gs, kBlock, 0, s>>>(S, val, rs, v, mv, zp, zb[k & 1], out, par_misc,
+                launch_pdl(k_rich_step<TA, VS, TC, TP>, dim3(c.Gs), dim3(kBlock), 0, s, S, val, rs, v, mv, zp, zb[k & 1], out, par_misc,
                                                                     R, k, last ? 1 : 0, c.flags, cd, n);
                 prof_end(c, s);
                 c.launches++;
@@ -70,12 +70,12 @@ static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const 
         const VS *rk = v;  // r_0 = v without an SpMV
         prof_begin(c, PK_RICH_UPD, 0, s);
         if (k > 0) {
-            k_rich_upd_r<TA, VS, TC><<<c.Gs, kBlock, 0, s>>>(S, val, rs, v, zp, r, c.flags, cd, n);
+            launch_pdl(k_rich_upd_r<TA, VS, TC>, dim3(c.Gs), dim3(kBlock), 0, s, S, val, rs, v, zp, r, c.flags, cd, n);
             rk = r;
             c.launches++;
         }
-        k_rich_upd_w<TA, VS, TC><<<c.Gs, kBlock, 0, s>>>(S, val, rs, rk, mv, R, k, pos, c.prm.c, gr, c.flags, cd, n);
-        k_rich_upd_z<VS, TC, TP><<<c.G, kBlock, 0, s>>>(rk, mv, zp, zb[k & 1], out, par_misc, R, last ? 1 : 0,
+        launch_pdl(k_rich_upd_w<TA, VS, TC>, dim3(c.Gs), dim3(kBlock), 0, s, S, val, rs, rk, mv, R, k, pos, c.prm.c, gr, c.flags, cd, n);
+        launch_pdl(k_rich_upd_z<VS, TC, TP>, dim3(c.G), dim3(kBlock), 0, s, rk, mv, zp, zb[k & 1], out, par_misc, R, last ? 1 : 0,
                                                        c.flags, cd, n);
         prof_end(c, s);
         c.launches += 2;
@@ -84,6 +84,12 @@ static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const 
 
 void launch_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s) {
     const int a = c.prm.rich_a_prec, v = c.prm.rich_v_prec;
+    if (c.prm.precond == F3R_PC_LEARNED && c.learned) {
+        prof_begin(c, PK_RICH_STEP, 1, s);
+        learned_rich_call(c, update, pos, out, par_misc, s);
+        prof_end(c, s);
+        return;
+    }
     if (v == F3R_F16 && a == F3R_F16)
         rich_go<h16, h16, float, float>(c, c.a16, update, pos, (float *)out, (const float *)par_misc, s);
     else if (v == F3R_BF16 && a == F3R_BF16)
@@ -100,23 +106,23 @@ void launch_rich_prep(Ctx &c, const void *x, cudaStream_t s) {
     const int ws = (c.prm.scale_cast && (c.prm.rich_v_prec == F3R_F16 || c.prm.rich_v_prec == F3R_BF16)) ? 1 : 0;
     if (p64) {
         GridRed<double> gr{(double *)c.partials, c.ticket, kMaxDots};
-        k_amax_sigma<double><<<c.G, kBlock, 0, s>>>((const double *)x, c.n, (double *)c.apply_misc, ws, gr);
-        k_cast_scaled<double, double><<<c.G, kBlock, 0, s>>>((const double *)x, (double *)c.rin, c.n,
+        launch_pdl(k_amax_sigma<double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)x, c.n, (double *)c.apply_misc, ws, gr);
+        launch_pdl(k_cast_scaled<double, double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)x, (double *)c.rin, c.n,
                                                               (const double *)c.apply_misc);
     } else {
         GridRed<float> gr{(float *)c.partials, c.ticket, kMaxDots};
-        k_amax_sigma<float><<<c.G, kBlock, 0, s>>>((const float *)x, c.n, (float *)c.apply_misc, ws, gr);
+        launch_pdl(k_amax_sigma<float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)x, c.n, (float *)c.apply_misc, ws, gr);
         switch (c.prm.rich_v_prec) {
             case F3R_F16:
-                k_cast_scaled<float, h16><<<c.G, kBlock, 0, s>>>((const float *)x, (h16 *)c.rin, c.n,
+                launch_pdl(k_cast_scaled<float, h16>, dim3(c.G), dim3(kBlock), 0, s, (const float *)x, (h16 *)c.rin, c.n,
                                                                  (const float *)c.apply_misc);
                 break;
             case F3R_BF16:
-                k_cast_scaled<float, b16><<<c.G, kBlock, 0, s>>>((const float *)x, (b16 *)c.rin, c.n,
+                launch_pdl(k_cast_scaled<float, b16>, dim3(c.G), dim3(kBlock), 0, s, (const float *)x, (b16 *)c.rin, c.n,
                                                                  (const float *)c.apply_misc);
                 break;
             default:
-                k_cast_scaled<float, float><<<c.G, kBlock, 0, s>>>((const float *)x, (float *)c.rin, c.n,
+                launch_pdl(k_cast_scaled<float, float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)x, (float *)c.rin, c.n,
                                                                    (const float *)c.apply_misc);
                 break;
         }

@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(kBlock) k_rich2(Sell S, const TA *__restrict__
                                                   const VS *__restrict__ v, const VS *__restrict__ mv, TP *out,
                                                   const TP *par_misc, RichDev<TC> R, const int *flags, int check_depth,
                                                   int n) {
+    pdl_enter();
     if (stopped(flags, check_depth)) return;
     const TC w1 = R.omega[0], w2 = R.omega[1];
     const TP inv_sigma = par_misc[MS_INV_SIGMA];
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(kBlock) k_rich_step(Sell S, const TA *__restri
                                                       const VS *__restrict__ zprev, VS *znext, TP *out,
                                                       const TP *par_misc, RichDev<TC> R, int k, int last,
                                                       const int *flags, int check_depth, int n) {
+    pdl_enter();
     if (stopped(flags, check_depth)) return;
     const TC wk = R.omega[k];
     const TP inv_sigma = par_misc[MS_INV_SIGMA];
@@ -98,6 +100,7 @@ template <class TA, class VS, class TC>
 __global__ void __launch_bounds__(kBlock) k_rich_upd_r(Sell S, const TA *__restrict__ val, const float *__restrict__ rs,
                                                        const VS *__restrict__ v, const VS *__restrict__ z, VS *r,
                                                        const int *flags, int check_depth, int n) {
+    pdl_enter();
     if (stopped(flags, check_depth)) return;
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -117,6 +120,7 @@ __global__ void __launch_bounds__(kBlock) k_rich_upd_w(Sell S, const TA *__restr
                                                        const VS *__restrict__ r, const VS *__restrict__ mv,
                                                        RichDev<TC> R, int k, int pos, int c, GridRed<TC> gr,
                                                        const int *flags, int check_depth, int n) {
+    pdl_enter();
     if (stopped(flags, check_depth)) return;
     TC acc[2] = {(TC)0, (TC)0};
     const int lane = threadIdx.x & 31;
@@ -153,6 +157,7 @@ __global__ void __launch_bounds__(kBlock) k_rich_upd_z(const VS *__restrict__ r,
                                                        const VS *__restrict__ zprev, VS *znext, TP *out,
                                                        const TP *par_misc, RichDev<TC> R, int last,
                                                        const int *flags, int check_depth, int n) {
+    pdl_enter();
     if (stopped(flags, check_depth)) return;
     const TC wp = *R.wcur;
     const TP inv_sigma = par_misc[MS_INV_SIGMA];
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(kBlock) k_rich_upd_z(const VS *__restrict__ r,
 template <class TP>
 __global__ void __launch_bounds__(kBlock) k_amax_sigma(const TP *v, int n, TP *misc, int want_sigma,
                                                        GridRed<TP> gr) {
+    pdl_enter();
     TP acc[1] = {(TP)0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         acc[0] = fmax(acc[0], fabs(v[i]));
@@ -188,6 +194,7 @@ __global__ void __launch_bounds__(kBlock) k_amax_sigma(const TP *v, int n, TP *m
 
 template <class TP, class VS>
 __global__ void __launch_bounds__(kBlock) k_cast_scaled(const TP *v, VS *out, int n, const TP *misc) {
+    pdl_enter();
     const TP sg = misc[MS_SIGMA];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         out[i] = Store<VS>::from(mul_rn(sg, v[i]));

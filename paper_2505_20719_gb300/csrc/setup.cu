@@ -3,6 +3,7 @@
 // fp64 / fp32 / fp16 / bf16 copies of the scaled matrix (Table 1).  Runs on
 // the device after one upload of the CSR arrays.
 #include <algorithm>
+#include <cstdlib>
 
 #include "ctx.h"
 #include "stage.cuh"
@@ -268,6 +269,14 @@ StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize) {
         }
     }
     return p;
+}
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char *e = getenv("F3R_PDL");
+        return e && e[0] == '1';
+    }();
+    return on;
 }
 
 int maxd_bucket(int m) { return m <= 4 ? 4 : (m <= 8 ? 8 : 16); }

@@ -73,7 +73,10 @@ f3r_status check_params(const f3r_params &p) {
     }
     if (p.c < 1 || p.max_outer < 1 || !(p.tol >= 0.0)) return F3R_ERR_ARG;
     if (p.cgs_passes != 1 && p.cgs_passes != 2) return F3R_ERR_ARG;
-    if (p.precond != F3R_PC_IDENTITY && p.precond != F3R_PC_JACOBI) return F3R_ERR_ARG;
+    if (p.precond != F3R_PC_IDENTITY && p.precond != F3R_PC_JACOBI && p.precond != F3R_PC_LEARNED) return F3R_ERR_ARG;
+    if (p.precond == F3R_PC_LEARNED &&
+        (p.rich_m < 1 || p.rich_v_prec != F3R_F16 || p.rich_a_prec != F3R_F16 || p.row_scale))
+        return F3R_ERR_UNSUPPORTED;
     return F3R_OK;
 }
 
@@ -162,6 +165,7 @@ void run_level(Ctx &c, int d, const OutSlot &out, long long &pos, cudaStream_t s
 
 __global__ void k_pack_readback(const double *misc0, const int *flags, const unsigned long long *counters,
                                 const int *err, Readback *rb) {
+    pdl_enter();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         rb->err = *err;
         rb->est = misc0[MS_EST];
@@ -174,7 +178,7 @@ __global__ void k_pack_readback(const double *misc0, const int *flags, const uns
 
 void pack_readback(f3r_ctx *h, cudaStream_t s) {
     Ctx &c = h->c;
-    k_pack_readback<<<1, 32, 0, s>>>((const double *)misc_of(c, 0), c.flags, c.counters, c.err, h->rb_dev);
+    launch_pdl(k_pack_readback, dim3(1), dim3(32), 0, s, (const double *)misc_of(c, 0), c.flags, c.counters, c.err, h->rb_dev);
     c.launches++;
     cudaMemcpyAsync(c.rb, h->rb_dev, sizeof(Readback), cudaMemcpyDeviceToHost, s);
 }
@@ -292,6 +296,7 @@ void f3r_destroy(f3r_ctx *h) {
     if (!h) return;
     Ctx &c = h->c;
     for (auto &kv : c.graphs) cudaGraphExecDestroy(kv.second);
+    learned_free(c);
     for (auto &r : c.prec) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -373,6 +378,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     c.G = std::max(1, std::min(ceil_div(n, kBlock), c.nsm * 4));
     c.Gs = std::max(1, std::min(ceil_div(c.nslices, kWarps), c.nsm * 4));
     c.G1 = std::max(1, std::min(ceil_div(n, 512), c.nsm));
+    c.Gv = std::max(1, std::min(ceil_div(n, 512 * 16), c.nsm * 2));
 
     // levels (Table 1)
     for (int d = 0; d < prm.nlevels; ++d) {
@@ -402,7 +408,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     c.c_ntr_base = (long long *)dalloc(c, sizeof(long long));
     c.zst = dalloc(c, sizeof(double) * c.ld);
     c.apply_misc = dalloc(c, sizeof(double) * MS_COUNT);
-    const size_t pbytes = std::max((size_t)c.nsm * 4 * kMaxDots * sizeof(double),
+    const size_t pbytes = std::max((size_t)c.nsm * 8 * kMaxDots * sizeof(double),
                                    (size_t)(kMaxOuterM + 2) * c.G1 * sizeof(double));
     c.partials = dalloc(c, pbytes);
     c.ticket = (unsigned *)dalloc(c, sizeof(unsigned) * 4);
@@ -646,6 +652,62 @@ const char *f3r_profile_slot_name(int slot) {
                                           "outer_spmv", "outer_cgs", "outer_other", "spmv"};
     if (slot < 0 || slot >= kProfSlots) return "";
     return names[slot / 4];
+}
+
+f3r_status f3r_learned_load(f3r_ctx *h, const float *params, int train) {
+    if (!h || !params) return F3R_ERR_ARG;
+    return learned_enable(h->c, params, train != 0);
+}
+
+f3r_status f3r_learned_get(f3r_ctx *h, float *out) {
+    if (!h || !out || !h->c.learned) return F3R_ERR_ARG;
+    return cudaMemcpy(out, learned_theta(h->c), sizeof(float) * F3R_LEARNED_NPARAMS, cudaMemcpyDeviceToHost) ==
+                   cudaSuccess
+               ? F3R_OK
+               : F3R_ERR_CUDA;
+}
+
+f3r_status f3r_learned_apply(f3r_ctx *h, const float *r, float *z, void *stream) {
+    if (!h || !r || !z || !h->c.learned) return F3R_ERR_ARG;
+    learned_forward(h->c, r, z, false, (cudaStream_t)stream);
+    return cudaGetLastError() == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
+}
+
+f3r_status f3r_learned_loss_grad(f3r_ctx *h, const float *R, const float *E, int P, float *loss, float *grad,
+                                 void *stream) {
+    if (!h || !R || !E || P < 1 || !h->c.learned) return F3R_ERR_ARG;
+    f3r_status st = learned_enable(h->c, nullptr, true);
+    if (st != F3R_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = learned_loss_grad(h->c, R, E, P, s);
+    if (st != F3R_OK) return st;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return F3R_ERR_CUDA;
+    if (loss) cudaMemcpy(loss, learned_loss(h->c), sizeof(float), cudaMemcpyDeviceToHost);
+    if (grad) cudaMemcpy(grad, learned_grad(h->c), sizeof(float) * F3R_LEARNED_NPARAMS, cudaMemcpyDeviceToHost);
+    return cudaGetLastError() == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
+}
+
+f3r_status f3r_learned_train(f3r_ctx *h, const float *R, const float *E, int P, int steps, int batch, float lr,
+                             float *loss_hist, void *stream) {
+    if (!h || !R || !E || P < 1 || steps < 0 || batch < 1 || batch > P || !h->c.learned) return F3R_ERR_ARG;
+    f3r_status st = learned_enable(h->c, nullptr, true);
+    if (st != F3R_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = h->c.n;
+    int p0 = 0;
+    for (int k = 0; k < steps; ++k) {
+        const int b = std::min(batch, P - p0);
+        st = learned_loss_grad(h->c, R + (size_t)p0 * n, E + (size_t)p0 * n, b, s);
+        if (st != F3R_OK) return st;
+        learned_adam(h->c, lr, s);
+        if (loss_hist) {
+            if (cudaMemcpyAsync(loss_hist + k, learned_loss(h->c), sizeof(float), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess)
+                return F3R_ERR_CUDA;
+        }
+        p0 = (p0 + b) % P;
+    }
+    return cudaStreamSynchronize(s) == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
 }
 
 f3r_status f3r_export(f3r_ctx *h, int which, void *out) {

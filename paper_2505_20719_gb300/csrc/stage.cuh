@@ -2,13 +2,13 @@
 // copies (TMA, cp.async.bulk) and mbarrier completion.
 //
 // A block walks a contiguous range of tiles (8 consecutive slices = 256
-// rows) through a ring of S shared-memory stages.  One thread issues, per
-// tile, one bulk copy for the tile's column indices, one for its values and
-// one per extra row-aligned vector segment (e.g. the Krylov basis rows the
-// fused dot products read), all completing on the stage's mbarrier.  S tiles
-// are in flight per block, which keeps enough bytes moving to cover HBM
-// latency while the warps gather x (largely from L1, since a block's tiles
-// are neighbours) and accumulate.
+// rows) through a ring of S shared-memory stages.  A producer warp issues,
+// per tile, one bulk copy for the tile's column indices, one for its values
+// and one per extra row-aligned vector segment (e.g. the Krylov basis rows
+// the fused dot products read), all completing on the stage's mbarrier.  S
+// tiles are in flight per block, which keeps enough bytes moving to cover HBM
+// latency while the consumer warps gather x (largely from L1, since a block's
+// tiles are neighbours) and accumulate.
 //
 // Every wait is bounded: after about two seconds of failed polls the kernel
 // records an error code, waits (bounded again) for its own copies still in
@@ -37,6 +37,11 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+
+// Order every earlier generic-proxy access (including the previous grid's
+// writes made visible by griddepcontrol.wait) before later async-proxy (TMA)
+// accesses of this thread.
+__device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -101,18 +106,27 @@ template <class TA> struct StageView {
     }
 };
 
-// Block-level ring of S stages over a contiguous range of tiles.  Thread 0
-// fills a stage with one bulk copy of the tile's column indices, one of its
-// values and one per extra vector; all warps wait on the stage's mbarrier,
-// warp w processes slice w of the tile, and after a block-wide barrier the
-// stage is refilled with the tile S ahead.  body(s, view) runs on all lanes of
-// the warp owning slice s.  The stop decision after a failed wait is
-// block-uniform (__syncthreads_or), so no warp is left at a barrier.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Warp-specialised ring of S stages over a contiguous range of tiles.  The
+// block has kWarps consumer warps and one producer warp (the last).  The
+// producer's lane 0 fills stage st with one bulk copy of the tile's column
+// indices, one of its values and one per extra vector, completing on
+// full[st]; consumer warp w waits on full[st], processes slice w of the tile
+// and arrives on empty[st]; the producer refills a stage once all consumers
+// released it.  Consumers therefore run up to S - 1 tiles apart without a
+// block-wide barrier.  body(s, view) runs on all lanes of the consumer warp
+// owning slice s.  Every wait is bounded; a consumer that gives up records
+// the error and stops, the producer stops refilling after a failed wait and
+// finally waits (bounded) for the copies it issued.
 template <class TA, int S, class Body>
 __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict__ val, int tile_begin,
-                                             int tile_end, char *ring, int stage_bytes, uint64_t *bars, Extra ex,
-                                             int *err, Body body) {
+                                             int tile_end, char *ring, int stage_bytes, uint64_t *full,
+                                             uint64_t *empty, Extra ex, int *err, Body body) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool producer = (warp == kWarps);
     auto issue = [&](int t, int st) {
         const int s0 = t * kTileSlices;
         const int s1 = min(s0 + kTileSlices, A.nslices);
@@ -120,9 +134,9 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
         const uint32_t colb = (uint32_t)(b1 - b0) * 4u;
         const uint32_t valb = (uint32_t)(b1 - b0) * (uint32_t)sizeof(TA);
         const uint32_t extb = (uint32_t)kTileRows * ex.esize;
-        const uint32_t bar = smem_u32(bars + st);
+        const uint32_t bar = smem_u32(full + st);
         const uint32_t dst = smem_u32(ring + (size_t)st * stage_bytes);
-        fence_proxy_async();  // earlier generic reads of this stage before the async refill
+        fence_proxy_async();  // the consumers' generic reads of this stage before the async refill
         mbar_expect_tx(bar, colb + valb + extb * ex.count);
         if (colb) {
             bulk_g2s(dst, A.col + b0, colb, bar);
@@ -133,47 +147,59 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
                      (const char *)ex.base + ((size_t)l * ex.ld + (size_t)t * kTileRows) * ex.esize, extb, bar);
     };
     if (threadIdx.x == 0) {
-        for (int st = 0; st < S; ++st) mbar_init(smem_u32(bars + st), 1);
+        for (int st = 0; st < S; ++st) {
+            mbar_init(smem_u32(full + st), 1);
+            mbar_init(smem_u32(empty + st), kWarps);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int st = 0; st < S; ++st)
-            if (tile_begin + st < tile_end) issue(tile_begin + st, st);
     bool ok = true;
-    int k = 0;
-    for (int t = tile_begin; t < tile_end; ++t, ++k) {
-        const int st = k % S;
-        const bool got = mbar_wait(smem_u32(bars + st), (uint32_t)((k / S) & 1));
-        if (__syncthreads_or(got ? 0 : 1)) {
-            ok = false;
-            break;
+    if (producer) {
+        fence_proxy_async_all();  // the basis rows the previous kernel wrote, before the first bulk copy
+        int k = 0;
+        for (int t = tile_begin; t < tile_end; ++t, ++k) {
+            const int st = k % S;
+            if (k >= S && !mbar_wait(smem_u32(empty + st), (uint32_t)(((k / S) - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            if (lane == 0) issue(t, st);
+            __syncwarp();
         }
-        const int s = t * kTileSlices + warp;
-        if (s < A.nslices) {
-            const char *base = ring + (size_t)st * stage_bytes;
-            const int bt = __ldg(A.sptr + t * kTileSlices);
-            const int tile_nnz = __ldg(A.sptr + min(t * kTileSlices + kTileSlices, A.nslices)) - bt;
-            const int b0 = __ldg(A.sptr + s), b1 = __ldg(A.sptr + s + 1);
-            StageView<TA> v;
-            v.w = (b1 - b0) >> 5;
-            v.col = reinterpret_cast<const int *>(base) + (b0 - bt);
-            v.val = reinterpret_cast<const TA *>(base + (size_t)tile_nnz * 4) + (b0 - bt);
-            v.extra = base + (size_t)tile_nnz * (4 + sizeof(TA));
-            v.esize = ex.esize;
-            v.row0 = warp * kSlice;
-            body(s, v);
+        // wait for the copies of the last (up to S) tiles issued, so none lands after exit
+        const int issued = k;
+        for (int kk = max(0, issued - S); kk < issued; ++kk)
+            mbar_wait(smem_u32(full + kk % S), (uint32_t)((kk / S) & 1));
+        if (!ok && lane == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
+    } else {
+        int k = 0;
+        for (int t = tile_begin; t < tile_end; ++t, ++k) {
+            const int st = k % S;
+            if (!mbar_wait(smem_u32(full + st), (uint32_t)((k / S) & 1))) {
+                ok = false;
+                if (lane == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
+                break;
+            }
+            const int s = t * kTileSlices + warp;
+            if (s < A.nslices) {
+                const char *base = ring + (size_t)st * stage_bytes;
+                const int bt = __ldg(A.sptr + t * kTileSlices);
+                const int tile_nnz = __ldg(A.sptr + min(t * kTileSlices + kTileSlices, A.nslices)) - bt;
+                const int b0 = __ldg(A.sptr + s), b1 = __ldg(A.sptr + s + 1);
+                StageView<TA> v;
+                v.w = (b1 - b0) >> 5;
+                v.col = reinterpret_cast<const int *>(base) + (b0 - bt);
+                v.val = reinterpret_cast<const TA *>(base + (size_t)tile_nnz * 4) + (b0 - bt);
+                v.extra = base + (size_t)tile_nnz * (4 + sizeof(TA));
+                v.esize = ex.esize;
+                v.row0 = warp * kSlice;
+                body(s, v);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(empty + st));
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && t + S < tile_end) issue(t + S, st);
     }
-    if (!ok) {
-        // record the failure, then drain the copies still in flight (bounded waits)
-        if (threadIdx.x == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
-        for (int kk = k; kk < k + S && tile_begin + kk < tile_end; ++kk)
-            mbar_wait(smem_u32(bars + kk % S), (uint32_t)((kk / S) & 1));
-    }
-    (void)lane;
     return ok;
 }
 

@@ -4,8 +4,9 @@
 // outer fp64 SpMV.  Each lane still sums its row in CSR order with fused
 // multiply-add, so results equal the unstaged kernels bit for bit.
 //
-// Dynamic shared memory per block: [S mbarriers, padded to 256 B]
-// [ring of S stages of `stage_bytes`].  Block b owns the contiguous tiles
+// Blocks have kWarps consumer warps plus one producer warp (kStagedThreads).
+// Dynamic shared memory per block: [S full + S empty mbarriers, padded to
+// 256 B][ring of S stages of `stage_bytes`].  Block b owns the contiguous tiles
 // [b * per, (b + 1) * per), per = ceil(tiles / gridDim.x).
 #pragma once
 #include "kernels.cuh"
@@ -15,6 +16,7 @@
 namespace f3r {
 
 constexpr int kBarBytes = 256;
+constexpr int kStagedThreads = kBlock + 32;
 
 struct StageCfg {
     int stage_bytes;
@@ -22,7 +24,8 @@ struct StageCfg {
 };
 
 __device__ __forceinline__ char *block_ring(char *dsm) { return dsm + kBarBytes; }
-__device__ __forceinline__ uint64_t *block_bars(char *dsm) { return reinterpret_cast<uint64_t *>(dsm); }
+__device__ __forceinline__ uint64_t *block_full(char *dsm) { return reinterpret_cast<uint64_t *>(dsm); }
+__device__ __forceinline__ uint64_t *block_empty(char *dsm) { return reinterpret_cast<uint64_t *>(dsm) + 8; }
 
 // this block's contiguous range of tiles
 __device__ __forceinline__ int2 tile_range(const Sell &A) {
@@ -47,9 +50,10 @@ __device__ __forceinline__ TC staged_row(const StageView<TA> &v, int lane, GX gx
 
 // w = A Z[j] (times the row scale), hA = V[0..j]^T w; V rows staged with the slice
 template <class TA, class T, int S, int MAXD>
-__global__ void __launch_bounds__(kBlock) k_spmv_dots_st(Sell A, const TA *__restrict__ val,
+__global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const TA *__restrict__ val,
                                                          const float *__restrict__ rs, LevelDev<T> L, int j,
                                                          GridRed<T> gr, StageCfg cfg) {
+    pdl_enter();
     if (stopped(L.flags, L.depth)) return;
     extern __shared__ __align__(128) char dsm[];
     const int lane = threadIdx.x & 31;
@@ -63,7 +67,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dots_st(Sell A, const TA *__res
     ex.ld = L.ld;
     ex.esize = sizeof(T);
     const int2 tr = tile_range(A);
-    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_bars(dsm), ex, cfg.err,
+    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), ex, cfg.err,
                         [&](int s, const StageView<TA> &v) {
                              T y = staged_row<T>(v, lane, [&](int c) { return __ldg(x + c); });
                              const int i = s * kSlice + lane;
@@ -83,17 +87,18 @@ __global__ void __launch_bounds__(kBlock) k_spmv_dots_st(Sell A, const TA *__res
 
 // fused plain Richardson call with m4 = 2 (see k_rich2)
 template <class TA, class VS, class TC, class TP, int S>
-__global__ void __launch_bounds__(kBlock) k_rich2_st(Sell A, const TA *__restrict__ val, const float *__restrict__ rs,
+__global__ void __launch_bounds__(kStagedThreads) k_rich2_st(Sell A, const TA *__restrict__ val, const float *__restrict__ rs,
                                                      const VS *__restrict__ v, const VS *__restrict__ mv, TP *out,
                                                      const TP *par_misc, RichDev<TC> R, const int *flags,
                                                      int check_depth, int n, StageCfg cfg) {
+    pdl_enter();
     if (stopped(flags, check_depth)) return;
     extern __shared__ __align__(128) char dsm[];
     const int lane = threadIdx.x & 31;
     const TC w1 = R.omega[0], w2 = R.omega[1];
     const TP inv_sigma = par_misc[MS_INV_SIGMA];
     const int2 tr = tile_range(A);
-    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_bars(dsm), Extra(), cfg.err,
+    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), Extra(), cfg.err,
                         [&](int s, const StageView<TA> &st) {
                              TC acc = staged_row<TC>(st, lane, [&](int c) {
                                  return rnd<VS>(fma_rn(w1, mul_rn(to_c<TC>(__ldg(mv + c)), to_c<TC>(__ldg(v + c))),
@@ -117,12 +122,13 @@ __global__ void __launch_bounds__(kBlock) k_rich2_st(Sell A, const TA *__restric
 
 // stand-alone y = A x
 template <class TA, class TX, class TY, int S>
-__global__ void __launch_bounds__(kBlock) k_spmv_st(Sell A, const TA *__restrict__ val, const float *__restrict__ rs,
+__global__ void __launch_bounds__(kStagedThreads) k_spmv_st(Sell A, const TA *__restrict__ val, const float *__restrict__ rs,
                                                     const TX *__restrict__ x, TY *y, StageCfg cfg) {
+    pdl_enter();
     extern __shared__ __align__(128) char dsm[];
     const int lane = threadIdx.x & 31;
     const int2 tr = tile_range(A);
-    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_bars(dsm), Extra(), cfg.err,
+    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), Extra(), cfg.err,
                         [&](int s, const StageView<TA> &st) {
                              TY acc = staged_row<TY>(st, lane, [&](int c) { return to_c<TY>(__ldg(x + c)); });
                              const int i = s * kSlice + lane;
@@ -133,14 +139,15 @@ __global__ void __launch_bounds__(kBlock) k_spmv_st(Sell A, const TA *__restrict
 
 // outer level: Z[j] = z (the inner nest's output) and w = A z, original fp64 A
 template <int S>
-__global__ void __launch_bounds__(kBlock) k_outer_spmv_st(Sell A, const double *__restrict__ a, LevelDev<double> L,
+__global__ void __launch_bounds__(kStagedThreads) k_outer_spmv_st(Sell A, const double *__restrict__ a, LevelDev<double> L,
                                                           const double *__restrict__ z, StageCfg cfg) {
+    pdl_enter();
     extern __shared__ __align__(128) char dsm[];
     const int lane = threadIdx.x & 31;
     const int j = *L.jptr;
     double *zj = L.Z + (size_t)j * L.ld;
     const int2 tr = tile_range(A);
-    staged_tiles<double, S>(A, a, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_bars(dsm), Extra(), cfg.err,
+    staged_tiles<double, S>(A, a, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), Extra(), cfg.err,
                             [&](int s, const StageView<double> &st) {
                                  const double y = staged_row<double>(st, lane, [&](int c) { return __ldg(z + c); });
                                  const int i = s * kSlice + lane;

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libf3r.so")
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
-PC_IDENTITY, PC_JACOBI = 0, 1
+PC_IDENTITY, PC_JACOBI, PC_LEARNED = 0, 1, 2
+LEARNED_NPARAMS = 6337
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "not converged",
           5: "breakdown", 6: "non-finite value", 7: "device wait timed out", 8: "unsupported"}
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE = 0, 1, 2, 3, 4, 5, 6
@@ -48,6 +49,17 @@ class Stats(C.Structure):
     ]
 
 
+class SystemDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("colidx", C.c_void_p),
+                ("val", C.c_void_p), ("nrhs", C.c_int32)]
+
+
+class BatchResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("restarts", C.c_int),
+                ("rel_res_true", C.c_double), ("m_applies", C.c_int64), ("r_calls", C.c_int64),
+                ("t_solve_ms", C.c_double), ("system", C.c_int), ("rhs", C.c_int)]
+
+
 _lib = None
 
 
@@ -78,6 +90,27 @@ def lib():
         L.f3r_profile_slots.restype = C.c_int
         L.f3r_profile_slot_name.argtypes = [C.c_int]
         L.f3r_profile_slot_name.restype = C.c_char_p
+        L.f3r_setup_batched.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(SystemDesc), C.POINTER(Params), vp]
+        L.f3r_setup_batched.restype = C.c_int
+        L.f3r_solve_batched.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(BatchResult), vp]
+        L.f3r_solve_batched.restype = C.c_int
+        L.f3r_batched_set_cluster.argtypes = [vp, C.c_int]
+        L.f3r_batched_set_cluster.restype = C.c_int
+        L.f3r_batched_autotune.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int), vp]
+        L.f3r_batched_autotune.restype = C.c_int
+        L.f3r_batched_instances.argtypes = [vp]
+        L.f3r_batched_instances.restype = C.c_int
+        L.f3r_batched_device_bytes.argtypes = [vp]
+        L.f3r_batched_device_bytes.restype = C.c_int64
+        L.f3r_destroy_batched.argtypes = [vp]
+        L.f3r_learned_load.argtypes = [vp, vp, C.c_int]
+        L.f3r_learned_get.argtypes = [vp, vp]
+        L.f3r_learned_apply.argtypes = [vp, vp, vp, vp]
+        L.f3r_learned_loss_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp]
+        L.f3r_learned_train.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, vp, vp]
+        for name in ("f3r_learned_load", "f3r_learned_get", "f3r_learned_apply", "f3r_learned_loss_grad",
+                     "f3r_learned_train"):
+            getattr(L, name).restype = C.c_int
         L.f3r_residual_noalloc.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.f3r_residual_noalloc.restype = C.c_int
         for name in ("f3r_default_params", "f3r_setup", "f3r_solve", "f3r_spmv", "f3r_apply",
@@ -245,6 +278,35 @@ class Solver:
         _check(lib().f3r_export(self.h, which, _ptr(out)), "f3r_export")
         return out
 
+    # ------------------------------------------------------------ learned M
+    def learned_load(self, params, train: bool = False):
+        """Load the flat fp32 parameter vector (LEARNED_NPARAMS values)."""
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == LEARNED_NPARAMS
+        _check(lib().f3r_learned_load(self.h, p.ctypes.data, 1 if train else 0), "f3r_learned_load")
+
+    def learned_get(self) -> np.ndarray:
+        out = np.empty(LEARNED_NPARAMS, np.float32)
+        _check(lib().f3r_learned_get(self.h, out.ctypes.data), "f3r_learned_get")
+        return out
+
+    def learned_apply(self, r, z, stream=None):
+        _check(lib().f3r_learned_apply(self.h, _ptr(r), _ptr(z), _stream(stream)), "f3r_learned_apply")
+
+    def learned_loss_grad(self, R, E, stream=None):
+        """R, E: device fp32 (P, n).  Returns (loss, grad)."""
+        loss = np.zeros(1, np.float32)
+        grad = np.zeros(LEARNED_NPARAMS, np.float32)
+        _check(lib().f3r_learned_loss_grad(self.h, _ptr(R), _ptr(E), R.shape[0], loss.ctypes.data, grad.ctypes.data,
+                                           _stream(stream)), "f3r_learned_loss_grad")
+        return float(loss[0]), grad
+
+    def learned_train(self, R, E, steps: int, batch: int, lr: float, stream=None) -> np.ndarray:
+        hist = np.zeros(max(steps, 1), np.float32)
+        _check(lib().f3r_learned_train(self.h, _ptr(R), _ptr(E), R.shape[0], steps, batch, lr, hist.ctypes.data,
+                                       _stream(stream)), "f3r_learned_train")
+        return hist[:steps]
+
     def profile(self, enable: bool):
         """Turn the per-kernel event profiler on (resetting it) or off."""
         _check(lib().f3r_profile_enable(self.h, 1 if enable else 0), "f3r_profile_enable")
@@ -263,3 +325,61 @@ class Solver:
     @property
     def device_bytes(self) -> int:
         return lib().f3r_device_bytes(self.h)
+
+
+class BatchedSolver:
+    """Many systems (each with nrhs right-hand sides) solved in one persistent
+    launch: f3r_setup_batched / f3r_solve_batched."""
+
+    def __init__(self, systems, params: Params = None, stream=None):
+        """systems: list of (rowptr, colidx, val, nrhs) with host (numpy) or
+        device (torch) arrays."""
+        self.h = C.c_void_p()
+        self._keep = systems
+        arr = (SystemDesc * len(systems))()
+        self.ns = []
+        for k, (rp, ci, va, nrhs) in enumerate(systems):
+            n = len(rp) - 1
+            self.ns.append(n)
+            arr[k] = SystemDesc(n, int(rp[-1]), _ptr(rp), _ptr(ci), _ptr(va), nrhs)
+        self.params = params if params is not None else default_params()
+        _check(lib().f3r_setup_batched(C.byref(self.h), len(systems), arr, C.byref(self.params),
+                                       _stream(stream)), "f3r_setup_batched")
+        self.ninst = lib().f3r_batched_instances(self.h)
+
+    def set_cluster(self, k: int):
+        _check(lib().f3r_batched_set_cluster(self.h, k), "f3r_batched_set_cluster")
+
+    def autotune(self, B, X, stream=None) -> int:
+        """Pick the cluster size by timing one outer iteration of the batch; X is zeroed."""
+        bp = (C.c_void_p * self.ninst)(*[b.data_ptr() for b in B])
+        xp = (C.c_void_p * self.ninst)(*[x.data_ptr() for x in X])
+        ch = C.c_int()
+        _check(lib().f3r_batched_autotune(self.h, bp, xp, C.byref(ch), _stream(stream)), "f3r_batched_autotune")
+        return ch.value
+
+    def solve(self, B, X, stream=None):
+        """B, X: lists (one per instance) of device fp64 tensors; X holds x0."""
+        assert len(B) == self.ninst and len(X) == self.ninst
+        bp = (C.c_void_p * self.ninst)(*[b.data_ptr() for b in B])
+        xp = (C.c_void_p * self.ninst)(*[x.data_ptr() for x in X])
+        res = (BatchResult * self.ninst)()
+        code = lib().f3r_solve_batched(self.h, bp, xp, res, _stream(stream))
+        if code not in (OK, NOT_CONVERGED, ERR_NONFINITE):
+            raise F3RError(code, "f3r_solve_batched")
+        return code, list(res)
+
+    @property
+    def device_bytes(self) -> int:
+        return lib().f3r_batched_device_bytes(self.h)
+
+    def close(self):
+        if self.h and _lib is not None:
+            _lib.f3r_destroy_batched(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,65 @@
+"""Batched F3R (many systems and right-hand sides in one persistent launch)
+against the single-system CUDA path and the CPU oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from problems import generators as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2505_20719_gb300 import f3r  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return G.batched_diffusion_systems(count=6, n_lo=500, n_hi=20000, max_rhs=3, seed=401)
+
+
+@pytest.mark.parametrize("cluster", [1, 2, 8])
+def test_batched_matches_single_system_solves(batch, cluster):
+    systems = [(dev(p.rowptr), dev(p.colidx), dev(p.val), B.shape[0]) for p, B in batch]
+    bs = f3r.BatchedSolver(systems, f3r.default_params())
+    bs.set_cluster(cluster)
+    Bs, Xs, meta = [], [], []
+    for k, (p, B) in enumerate(batch):
+        for r in range(B.shape[0]):
+            Bs.append(dev(B[r]))
+            Xs.append(torch.zeros(p.n, dtype=torch.float64, device="cuda"))
+            meta.append((k, r))
+    code, res = bs.solve(Bs, Xs)
+    torch.cuda.synchronize()
+    assert code == f3r.OK
+    for q, (k, r) in enumerate(meta):
+        p, B = batch[k]
+        A = p.to_scipy()
+        x = Xs[q].cpu().numpy()
+        rel = np.linalg.norm(B[r] - A @ x) / np.linalg.norm(B[r])
+        assert res[q].status == f3r.OK and res[q].system == k and res[q].rhs == r
+        assert rel < 1e-9 and abs(rel - res[q].rel_res_true) <= 1e-12
+        assert res[q].m_applies == 64 * res[q].outer_iters
+        s = f3r.Solver(dev(p.rowptr), dev(p.colidx), dev(p.val), f3r.default_params())
+        xs = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+        rs = s.solve(dev(B[r]), xs)
+        assert abs(rs.outer_iters - res[q].outer_iters) <= 1
+        s.close()
+    bs.close()
+
+
+def test_batched_instance_matches_oracle(batch):
+    p, B = batch[0]
+    bs = f3r.BatchedSolver([(dev(p.rowptr), dev(p.colidx), dev(p.val), 1)], f3r.default_params())
+    x = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+    code, res = bs.solve([dev(B[0])], [x])
+    ref = O.Problem(p).solve(O.params(), B[0])
+    assert code == f3r.OK and ref.status == O.OK
+    assert abs(res[0].outer_iters - ref.outer_iters) <= max(1, ref.outer_iters // 10)
+    assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-6 * np.linalg.norm(ref.x)

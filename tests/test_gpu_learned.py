@@ -1,0 +1,109 @@
+"""Learned preconditioner M_theta on the GPU against the CPU oracle
+(oracle/learned.py): forward in bf16 storage, gradients, training and use as
+M inside the fp16 Richardson level."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import learned as LM
+from problems import generators as G
+from problems import learned_init as LI
+from problems import rng
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2505_20719_gb300 import f3r  # noqa: E402
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def setup():
+    prob = G.diffusion27_nodal(dims=(13, 12, 11), seed=701)  # n = 1716: ragged 16-node groups and slices
+    s = f3r.Solver(dev(prob.rowptr), dev(prob.colidx), dev(prob.val), f3r.default_params())
+    P = O.Problem(prob, diag_scale=1)
+    # the fp16 copy of A^ the net aggregates over
+    A16 = LM.offdiag(P.get("a16"), prob.rowptr, prob.colidx, prob.n)
+    return prob, s, A16
+
+
+def _cos(a, b):
+    return float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300))
+
+
+def test_forward_matches_oracle_bf16(setup):
+    prob, s, A16 = setup
+    p = LI.init_params(readout_scale=0.5)
+    s.learned_load(LI.flatten(p).astype(np.float32))
+    for seed in (1, 2):
+        r = rng.normal(seed, 7, prob.n).astype(np.float32)
+        z = torch.empty(prob.n, dtype=torch.float32, device="cuda")
+        s.learned_apply(dev(r), z)
+        torch.cuda.synchronize()
+        pf = LI.unflatten(LI.flatten(p).astype(np.float32).astype(np.float64))
+        want, _ = LM.forward(A16, r.astype(np.float64), pf, bf16=True)
+        got = z.cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(got - want) <= 1e-2 * np.linalg.norm(want)
+    # an untrained read-out (wo = 0, omega_j = 1) is Jacobi on A^ (diag = 1): z = r exactly
+    s.learned_load(LI.flatten(LI.init_params(readout_scale=0.0)).astype(np.float32))
+    r = rng.normal(3, 7, prob.n).astype(np.float32)
+    z = torch.empty(prob.n, dtype=torch.float32, device="cuda")
+    s.learned_apply(dev(r), z)
+    torch.cuda.synchronize()
+    assert np.array_equal(z.cpu().numpy(), r)
+
+
+def test_gradient_matches_oracle(setup):
+    prob, s, A16 = setup
+    p = LI.init_params(readout_scale=0.5)
+    flat = LI.flatten(p).astype(np.float32)
+    s.learned_load(flat, train=True)
+    R = rng.normal(11, 7, 2 * prob.n).reshape(2, prob.n).astype(np.float32)
+    E = rng.normal(12, 7, 2 * prob.n).reshape(2, prob.n).astype(np.float32)
+    loss, grad = s.learned_loss_grad(dev(R), dev(E))
+    pf = LI.unflatten(flat.astype(np.float64))
+    want_loss, want = LM.loss_and_grad(A16, pf, R.astype(np.float64), E.astype(np.float64))
+    assert abs(loss - want_loss) <= 2e-2 * want_loss
+    g = LI.unflatten(grad.astype(np.float64))
+    for k in LI.PARAM_ORDER:
+        a, b = np.ravel(g[k]), np.ravel(want[k])
+        assert _cos(a, b) >= 0.99, k
+        assert np.linalg.norm(a - b) <= 0.15 * np.linalg.norm(b) + 1e-6, k
+
+
+def test_training_reduces_loss_and_solves(setup):
+    prob, s, A16 = setup
+    n = prob.n
+    # (residual, correction) pairs from the fp64 solver: A^ e = r in the scaled system
+    s64 = f3r.Solver(dev(prob.rowptr), dev(prob.colidx), dev(prob.val), f3r.preset("fp64-F3R", tol=1e-11))
+    d = s64.export(0)  # D^-1/2
+    R, E = [], []
+    for k in range(8):
+        r = rng.normal(20 + k, 7, n)
+        x = np.zeros(n)
+        s64.solve(np.ascontiguousarray(r / d), x)  # A x = D^1/2 r  <=>  A^ (D^-1/2 x) ... e = x / d
+        R.append(r)
+        E.append(x / d)
+    R = np.array(R, np.float32)
+    E = np.array(E, np.float32)
+    s.learned_load(LI.flatten(LI.init_params(readout_scale=0.0)).astype(np.float32), train=True)
+    l0, _ = s.learned_loss_grad(dev(R), dev(E))
+    hist = s.learned_train(dev(R), dev(E), steps=150, batch=4, lr=3e-3)
+    l1, _ = s.learned_loss_grad(dev(R), dev(E))
+    assert np.all(np.isfinite(hist)) and l1 < 0.9 * l0
+    # the trained net as M inside the fp16 Richardson level: the fp64 outer level judges
+    theta = s.learned_get()
+    sl = f3r.Solver(dev(prob.rowptr), dev(prob.colidx), dev(prob.val), f3r.default_params(precond=f3r.PC_LEARNED))
+    sl.learned_load(theta)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    res = sl.solve(dev(prob.b), x)
+    A = prob.to_scipy()
+    rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+    assert res.status == f3r.OK and rel < 1e-9
+    assert res.m_applies == 64 * res.outer_iters
