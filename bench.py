@@ -35,6 +35,8 @@ WORKLOADS = {
     "convdiff27_160": "nonsymmetric 3-D 27-point convection-diffusion 160^3, cell Peclet in [0.1,10]",
     "poisson2d_64": "2-D 5-point Poisson 64x64, Jacobi M unscaled",
     "batched64": "64 uneven 2-D/3-D diffusion systems (n log-uniform in [1e4, 5e5]), 1-8 right-hand sides each",
+    "learned27": "learned message-passing M vs Jacobi inside fp16-F3R: trained on the 100^3 27-point nodal "
+                 "diffusion system, evaluated on 160^3 (log-normal nodal field, sigma 1.5)",
 }
 
 
@@ -255,6 +257,84 @@ def run_batched(args):
     return 0
 
 
+def run_learned(args):
+    """Learned preconditioner (a 3-layer message-passing net) against Jacobi as
+    the M of the fp16 Richardson level: train on 100^3 with pairs (r, A^-1 r)
+    from the fp64 solver (r seeded normal vectors), then time fp16-F3R to 1e-9
+    on 160^3 with each M."""
+    import torch
+    from paper_2505_20719_gb300 import f3r
+    from problems import generators as G
+    from problems import learned_init as LI
+    from problems import rng
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    tr = G.diffusion27_nodal(100)
+    n = tr.n
+    s64 = f3r.Solver(T(tr.rowptr), T(tr.colidx), T(tr.val), f3r.preset("fp64-F3R", tol=1e-10))
+    d = s64.export(0)  # D^-1/2: A^ e = r  <=>  A (D^-1/2 e) = D^1/2 r
+    npairs = 16
+    R = torch.empty(npairs, n, dtype=torch.float32, device=dev)
+    E = torch.empty(npairs, n, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    for k in range(npairs):
+        r = rng.normal(900 + k, 7, n)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+        s64.solve(T(r / d), x)
+        R[k] = T(r).float()
+        E[k] = (x / T(d)).float()
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t0
+    s64.close()
+    st = f3r.Solver(T(tr.rowptr), T(tr.colidx), T(tr.val), f3r.default_params(precond=f3r.PC_LEARNED))
+    st.learned_load(LI.flatten(LI.init_params(readout_scale=0.0)).astype(np.float32), train=True)
+    loss0, _ = st.learned_loss_grad(R, E)
+    steps = 400
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hist = st.learned_train(R, E, steps=steps, batch=4, lr=2e-3)
+    e1.record()
+    e1.synchronize()
+    t_train = e0.elapsed_time(e1)
+    loss1, _ = st.learned_loss_grad(R, E)
+    theta = st.learned_get()
+    st.close()
+    del R, E
+    ev = G.by_name("diffusion27_160")
+    b = T(ev.b)
+    out = {}
+    for name, prm in (("jacobi", f3r.default_params()), ("learned", f3r.default_params(precond=f3r.PC_LEARNED))):
+        s = f3r.Solver(T(ev.rowptr), T(ev.colidx), T(ev.val), prm)
+        if name == "learned":
+            s.learned_load(theta)
+        x = torch.zeros(ev.n, dtype=torch.float64, device=dev)
+        s.solve(b, x)  # warm-up (graphs)
+        times = []
+        for _ in range(max(1, args.steps)):
+            x.zero_()
+            e0.record()
+            r = s.solve(b, x)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        out[name] = {"ms": statistics.median(times), "outer_iters": r.outer_iters,
+                     "status": f3r.STATUS.get(r.status), "rel_res": r.rel_res_true,
+                     "ms_per_outer": statistics.median(times) / max(1, r.outer_iters)}
+        s.close()
+    res = {"metric": "learned M vs Jacobi in fp16-F3R: time-to-solution at 1e-9 (160^3 27-pt nodal diffusion)",
+           "value": out["learned"]["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+           "higher_is_better": False, "data": "synthetic",
+           "config": {"workload": "learned27", "desc": WORKLOADS["learned27"], "train_n": n, "eval_n": ev.n,
+                      "eval_nnz": ev.nnz, "pairs": npairs, "train_steps": steps, "batch": 4, "lr": 2e-3},
+           "learned": out["learned"], "jacobi": out["jacobi"],
+           "speedup_vs_jacobi": out["jacobi"]["ms"] / out["learned"]["ms"],
+           "train": {"loss_initial": loss0, "loss_final": loss1, "loss_hist_first_last": [float(hist[0]), float(hist[-1])],
+                     "train_ms": t_train, "pairs_s": t_pairs}}
+    print(json.dumps(res))
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -301,12 +381,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fuse-cgs", type=int, default=1, choices=[0, 1],
+                    help="1: CGS2 + normalisation of each inner iteration in one cooperative launch")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched64":
         return run_batched(args)
+    if args.workload == "learned27":
+        return run_learned(args)
 
     import torch
     from paper_2505_20719_gb300 import f3r
@@ -323,7 +407,7 @@ def main():
     ds = 0 if args.workload == "poisson2d_64" else 1
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     rp, ci, va, b = T(prob.rowptr), T(prob.colidx), T(prob.val), T(prob.b)
-    prm = f3r.preset(args.kind, diag_scale=ds)
+    prm = f3r.preset(args.kind, diag_scale=ds, fuse_cgs=args.fuse_cgs)
     s = f3r.Solver(rp, ci, va, prm, stream=stream)
     x = torch.zeros(prob.n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

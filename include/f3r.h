@@ -78,7 +78,11 @@ typedef struct {
     int max_outer;      /* total outer iterations before F3R_NOT_CONVERGED (Sec. 5: 300) */
     int use_graphs;     /* 1: replay each outer iteration as one CUDA graph */
     int keep_omega;     /* 1: keep the Richardson weights and counter of the previous solve */
-    int reserved[7];
+    int fuse_cgs;       /* 1: second CGS pass, norm, Givens step and normalisation of an inner
+                           iteration in one cooperative launch (when a block's rows fit in
+                           shared memory); 0: three launches.  Same arithmetic per row; only
+                           the summation order of the dot products differs. */
+    int reserved[6];
 } f3r_params;
 
 typedef struct {

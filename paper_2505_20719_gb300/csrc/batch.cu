@@ -195,12 +195,21 @@ __device__ __forceinline__ TC row_sum(const Sys &S, const TA *val, int s, int la
     const int beg = __ldg(S.sptr + s) + lane;
     const int w = (__ldg(S.sptr + s + 1) - __ldg(S.sptr + s)) >> 5;
     TC acc = (TC)0;
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-        const int idx = beg + (k << 5);
-        const int c = __ldg(S.col + idx);
-        const TA a = __ldg(val + idx);
-        if (c >= 0) acc = fma_rn(to_c<TC>(a), gx(c), acc);
+    constexpr int U = 4;  // loads of a group of entries issued before its multiply-adds
+    for (int k0 = 0; k0 < w; k0 += U) {
+        int c[U];
+        TC a[U], xv[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const int idx = beg + ((k0 + q) << 5);
+            c[q] = (k0 + q < w) ? __ldg(S.col + idx) : -1;
+            a[q] = (k0 + q < w) ? to_c<TC>(__ldg(val + idx)) : (TC)0;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) xv[q] = (c[q] >= 0) ? gx(c[q]) : (TC)0;
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+            if (c[q] >= 0) acc = fma_rn(a[q], xv[q], acc);
     }
     return acc;
 }

@@ -37,7 +37,7 @@ struct OutSlot {
 // Kernel timing slots (kind * 4 + level) for the event profiler.
 enum {
     PK_SPMV_DOTS = 0, PK_CGS_PASS, PK_CGS_FINAL, PK_NORMALIZE, PK_COMBINE, PK_START, PK_M, PK_RICH2,
-    PK_RICH_STEP, PK_RICH_UPD, PK_OUTER_SPMV, PK_OUTER_CGS, PK_OUTER_OTHER, PK_SPMV, PK_KINDS
+    PK_RICH_STEP, PK_RICH_UPD, PK_OUTER_SPMV, PK_OUTER_CGS, PK_OUTER_OTHER, PK_SPMV, PK_CGS_FUSED, PK_KINDS
 };
 constexpr int kProfSlots = PK_KINDS * 4;
 
@@ -46,8 +46,15 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
+// Launch shape of the fused CGS2 / normalisation kernel of one level
+// (G == 0: not fused).
+struct FusedPlan {
+    int G = 0, chunk = 0, smem = 0;
+};
+
 struct Ctx {
     int dev = 0, nsm = 0;
+    cudaStream_t zstream = nullptr;  // the context's stream (zero-fills of allocations)
     f3r_params prm{};
     int n = 0;
     long long nnz = 0;
@@ -77,6 +84,8 @@ struct Ctx {
     // reductions and flags
     void *partials = nullptr;
     unsigned *ticket = nullptr;
+    unsigned *coop = nullptr;   // grid-barrier counters of cooperative launches (zero between launches)
+    FusedPlan fplan[4];
     int G = 1, Gs = 1, G1 = 1, Gv = 1;  // grids: elementwise, SpMV, outer CGS, streaming vector kernels
     int *flags = nullptr;       // 4 ints per level
     int *err = nullptr;         // device error word (bounded waits that gave up)
@@ -143,10 +152,14 @@ void launch_normalize(Ctx &c, int d, bool from_w, int dst, cudaStream_t s);
 void launch_spmv_dots(Ctx &c, int d, int j, cudaStream_t s);
 void launch_cgs_pass(Ctx &c, int d, int j, cudaStream_t s);
 void launch_cgs_final(Ctx &c, int d, int j, bool last, cudaStream_t s);
+// launch_fused.cu
+void plan_cgs_fused(Ctx &c);
+bool launch_cgs_fused(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_t s);
+bool launch_outer_cgs_fused(Ctx &c, cudaStream_t s);
 void launch_combine(Ctx &c, int d, const OutSlot &o, cudaStream_t s);
 void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s);
 void launch_outer_residual(Ctx &c, const double *b, const double *x, bool compute_nb, cudaStream_t s);
-void launch_outer_step(Ctx &c, cudaStream_t s);
+bool launch_outer_step(Ctx &c, cudaStream_t s);
 void launch_outer_finish(Ctx &c, double *x, cudaStream_t s);
 void launch_advance(Ctx &c, long long inc, cudaStream_t s);
 f3r_status launch_spmv(Ctx &c, int p, int vp, const void *x, void *y, cudaStream_t s);

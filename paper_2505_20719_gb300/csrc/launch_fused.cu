@@ -1,0 +1,204 @@
+// Launcher of the fused CGS2 / Givens / normalisation kernel (k_cgs_fused):
+// one cooperative launch whose blocks each keep a contiguous chunk of w in
+// shared memory, or `false` when the chunks do not fit (the caller then uses
+// the three separate kernels).
+#include "ctx.h"
+#include "fused.cuh"
+
+namespace f3r {
+
+namespace {
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_coop(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                        Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// 2 blocks of 512 threads per SM when the chunk fits, else 1; every block of
+// the grid must be resident at once (the launch is cooperative)
+template <class K> FusedPlan fused_plan(const Ctx &c, K kern, int tsize) {
+    FusedPlan p;
+    for (int bps = 2; bps >= 1; --bps) {
+        const int G = c.nsm * bps;
+        const int per = ceil_div(c.n, G);
+        const int chunk = ceil_div(per, kFusedChunkAlign) * kFusedChunkAlign;
+        const int smem = chunk * tsize;
+        if (smem > 200 * 1024) continue;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kFusedThreads, smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (nb < bps) continue;
+        p.G = ceil_div(c.n, chunk);
+        p.chunk = chunk;
+        p.smem = smem;
+        return p;
+    }
+    return p;
+}
+
+template <class T> LevelDev<T> levdev_inner(Ctx &c, int d) {
+    LevelDev<T> L;
+    L.n = c.n;
+    L.ld = c.ld;
+    L.m = c.L[d].m;
+    L.depth = d;
+    L.V = (T *)c.L[d].V;
+    L.Z = (T *)c.L[d].Z;
+    L.w = (T *)c.L[d].w;
+    L.scal = (T *)c.L[d].scal;
+    L.flags = c.flags;
+    L.jptr = nullptr;
+    return L;
+}
+
+int want_sigma_of(const Ctx &c, int d) {
+    const bool rich_half = c.prm.rich_m > 0 && (c.prm.rich_v_prec == F3R_F16 || c.prm.rich_v_prec == F3R_BF16);
+    return (c.L[d].child == CHILD_R && rich_half && c.prm.scale_cast) ? 1 : 0;
+}
+
+// plan_only: size the launch of level d into c.fplan[d] (at set-up, outside
+// any stream capture); else launch with that plan
+template <class T, class TC, int CHILD, int MAXD>
+bool fused_go(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_t s, bool plan_only) {
+    auto kern = k_cgs_fused<T, TC, CHILD, MAXD>;
+    if (plan_only) {
+        c.fplan[d] = fused_plan(c, kern, (int)sizeof(T));
+        return c.fplan[d].G > 0;
+    }
+    const FusedPlan p = c.fplan[d];
+    if (p.G == 0) return false;
+    ChildOut<TC> co{};
+    if (CHILD == CHILD_F) {
+        co.x = (TC *)c.L[d + 1].V;
+        co.dsc = nullptr;
+        co.cscal = c.L[d + 1].scal;
+        co.cm = c.L[d + 1].m;
+        co.cdepth = d + 1;
+        co.want_sigma = want_sigma_of(c, d + 1);
+    } else if (CHILD == CHILD_R) {
+        co.x = (TC *)c.rin;
+    }
+    FusedScratch<T> fs{(T *)c.partials, c.coop, c.err, p.chunk};
+    GridRed<TC> grc{(TC *)c.partials, c.ticket, kMaxDots};
+    return launch_coop(kern, dim3(p.G), dim3(kFusedThreads), p.smem, s, levdev_inner<T>(c, d), j,
+                       c.prm.cgs_passes, last ? 1 : 0, want_sigma_of(c, d), do_norm ? 1 : 0, co, fs, grc) ==
+           cudaSuccess;
+}
+
+template <class T, class TC, int CHILD>
+bool fused_md(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_t s, bool plan_only) {
+    const int md = maxd_bucket(c.L[d].m);
+    if (md == 4) return fused_go<T, TC, CHILD, 4>(c, d, j, last, do_norm, s, plan_only);
+    if (md == 8) return fused_go<T, TC, CHILD, 8>(c, d, j, last, do_norm, s, plan_only);
+    return fused_go<T, TC, CHILD, 16>(c, d, j, last, do_norm, s, plan_only);
+}
+
+bool fused_dispatch(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_t s, bool plan_only) {
+    const bool t64 = c.L[d].v_prec == F3R_F64;
+    const int ch = c.L[d].child;
+    if (ch == CHILD_F) {
+        const bool c64 = c.L[d + 1].v_prec == F3R_F64;
+        if (t64 && c64) return fused_md<double, double, CHILD_F>(c, d, j, last, do_norm, s, plan_only);
+        if (t64) return fused_md<double, float, CHILD_F>(c, d, j, last, do_norm, s, plan_only);
+        if (c64) return fused_md<float, double, CHILD_F>(c, d, j, last, do_norm, s, plan_only);
+        return fused_md<float, float, CHILD_F>(c, d, j, last, do_norm, s, plan_only);
+    }
+    if (ch == CHILD_R) {
+        switch (c.prm.rich_v_prec) {
+            case F3R_F64: return fused_md<double, double, CHILD_R>(c, d, j, last, do_norm, s, plan_only);
+            case F3R_F32:
+                return t64 ? fused_md<double, float, CHILD_R>(c, d, j, last, do_norm, s, plan_only)
+                           : fused_md<float, float, CHILD_R>(c, d, j, last, do_norm, s, plan_only);
+            case F3R_F16:
+                return t64 ? fused_md<double, h16, CHILD_R>(c, d, j, last, do_norm, s, plan_only)
+                           : fused_md<float, h16, CHILD_R>(c, d, j, last, do_norm, s, plan_only);
+            default:
+                return t64 ? fused_md<double, b16, CHILD_R>(c, d, j, last, do_norm, s, plan_only)
+                           : fused_md<float, b16, CHILD_R>(c, d, j, last, do_norm, s, plan_only);
+        }
+    }
+    return t64 ? fused_md<double, double, CHILD_M>(c, d, j, last, do_norm, s, plan_only)
+               : fused_md<float, float, CHILD_M>(c, d, j, last, do_norm, s, plan_only);
+}
+
+template <class TC, int CHILD> bool outer_go(Ctx &c, cudaStream_t s, bool plan_only) {
+    auto kern = k_outer_cgs_fused<TC, CHILD>;
+    if (plan_only) {
+        c.fplan[0] = fused_plan(c, kern, (int)sizeof(double));
+        return c.fplan[0].G > 0;
+    }
+    const FusedPlan p = c.fplan[0];
+    if (p.G == 0) return false;
+    ChildOut<TC> co{};
+    if (CHILD == CHILD_F) {
+        co.x = (TC *)c.L[1].V;
+        co.dsc = c.prm.diag_scale ? c.dsc : nullptr;
+        co.cscal = c.L[1].scal;
+        co.cm = c.L[1].m;
+        co.cdepth = 1;
+        co.want_sigma = want_sigma_of(c, 1);
+    }
+    LevelDev<double> L = levdev_inner<double>(c, 0);
+    L.jptr = c.jdev;
+    FusedScratch<double> fs{(double *)c.partials, c.coop, c.err, p.chunk};
+    GridRed<TC> grc{(TC *)c.partials, c.ticket, kMaxDots};
+    return launch_coop(kern, dim3(p.G), dim3(kFusedThreads), p.smem, s, L, c.prm.cgs_passes, co, fs, grc) ==
+           cudaSuccess;
+}
+
+// the outer level's child: an FGMRES level (fp32 or fp64 vectors) or M; a
+// Richardson child keeps the separate kernels
+bool outer_dispatch(Ctx &c, cudaStream_t s, bool plan_only) {
+    const int ch = c.L[0].child;
+    if (ch == CHILD_F)
+        return c.L[1].v_prec == F3R_F64 ? outer_go<double, CHILD_F>(c, s, plan_only)
+                                        : outer_go<float, CHILD_F>(c, s, plan_only);
+    if (ch == CHILD_M) return outer_go<double, CHILD_M>(c, s, plan_only);
+    return false;
+}
+
+}  // namespace
+
+void plan_cgs_fused(Ctx &c) {
+    for (int d = 0; d < 4; ++d) c.fplan[d] = FusedPlan{};
+    if (!c.prm.fuse_cgs || !c.coop) return;
+    outer_dispatch(c, nullptr, true);
+    for (int d = 1; d < c.prm.nlevels; ++d) fused_dispatch(c, d, 0, false, false, nullptr, true);
+}
+
+bool launch_outer_cgs_fused(Ctx &c, cudaStream_t s) {
+    if (c.fplan[0].G == 0) return false;
+    prof_begin(c, PK_OUTER_CGS, 0, s);
+    outer_dispatch(c, s, false);
+    prof_end(c, s);
+    c.launches++;
+    return true;
+}
+
+bool launch_cgs_fused(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_t s) {
+    if (d < 1 || d > 3 || c.fplan[d].G == 0) return false;
+    prof_begin(c, PK_CGS_FUSED, d, s);
+    fused_dispatch(c, d, j, last, do_norm, s, false);
+    prof_end(c, s);
+    c.launches++;
+    return true;
+}
+
+}  // namespace f3r

@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kBlock) k_outer_store_z(LevelDev<double> L, co
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) dst[i] = z[i];
 }
 
-void launch_outer_step(Ctx &c, cudaStream_t s) {
+// returns true when the fused kernel also normalised V[j+1] (and advanced j)
+bool launch_outer_step(Ctx &c, cudaStream_t s) {
     LevelDev<double> L = levdev<double>(c, 0);
     prof_begin(c, PK_OUTER_SPMV, 0, s);
     const StagePlan pl = plan_stage(c, sizeof(double), 0, 8);
@@ -294,6 +295,7 @@ void launch_outer_step(Ctx &c, cudaStream_t s) {
         launch_pdl(k_outer_spmv, dim3(c.Gs), dim3(kBlock), 0, s, sell_of(c), c.a64, L);
     }
     prof_end(c, s);
+    if (launch_outer_cgs_fused(c, s)) return true;
     double *part = (double *)c.partials;
     prof_begin(c, PK_OUTER_CGS, 0, s);
     launch_pdl(k_outer_cgs<0>, dim3(c.G1), dim3(512), 0, s, L, c.prm.cgs_passes, part, c.ticket);
@@ -305,6 +307,7 @@ void launch_outer_step(Ctx &c, cudaStream_t s) {
     launch_pdl(k_outer_cgs<2>, dim3(c.G1), dim3(512), 0, s, L, c.prm.cgs_passes, part, c.ticket);
     prof_end(c, s);
     c.launches++;
+    return false;
 }
 
 void launch_outer_finish(Ctx &c, double *x, cudaStream_t s) {

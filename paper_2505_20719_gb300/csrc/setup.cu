@@ -258,8 +258,13 @@ StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize) {
     const int sb = stage_bytes_for(c.wmax, asize, n_extra, esize);
     // 3 stages if four blocks fit an SM, else 2 stages with two blocks, else
     // 2 stages with one block; wider tiles run unstaged.
+    static const int force_s = [] {
+        const char *e = getenv("F3R_STAGES");  // 2 or 3: ring depth override for tuning runs
+        return e ? atoi(e) : 0;
+    }();
     const int cand[3][2] = {{3, 56 * 1024}, {2, 110 * 1024}, {2, 220 * 1024}};
     for (auto &cs : cand) {
+        if (force_s == 2 && cs[0] == 3) continue;
         const int smem = 256 + cs[0] * sb;
         if (smem <= cs[1]) {
             p.S = cs[0];

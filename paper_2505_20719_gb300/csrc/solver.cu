@@ -37,13 +37,15 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// device allocation, zero-filled in the context's stream (so the fill is
+// ordered before every later use in that stream, unlike a legacy-stream memset)
 void *dalloc(Ctx &c, size_t bytes) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
     if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
     c.allocs.push_back(p);
     c.bytes += (long long)bytes;
-    cudaMemset(p, 0, bytes);
+    cudaMemsetAsync(p, 0, bytes, c.zstream);
     return p;
 }
 
@@ -156,6 +158,7 @@ void run_level(Ctx &c, int d, const OutSlot &out, long long &pos, cudaStream_t s
             launch_M(c, d, j, vslot(c, d, j), zslot(c, d, j), d, false, s);
         }
         launch_spmv_dots(c, d, j, s);
+        if (launch_cgs_fused(c, d, j, j == L.m - 1, j < L.m - 1, s)) continue;
         if (c.prm.cgs_passes == 2) launch_cgs_pass(c, d, j, s);
         launch_cgs_final(c, d, j, j == L.m - 1, s);
         if (j < L.m - 1) launch_normalize(c, d, true, j + 1, s);
@@ -200,8 +203,7 @@ void outer_iteration_body(f3r_ctx *h, cudaStream_t s) {
     } else {
         launch_M(c, 0, 0, c.L[0].V, c.zst, 0, true, s);
     }
-    launch_outer_step(c, s);
-    launch_normalize(c, 0, true, 1, s);
+    if (!launch_outer_step(c, s)) launch_normalize(c, 0, true, 1, s);
     if (c.calls_per_outer) launch_advance(c, c.calls_per_outer, s);
     pack_readback(h, s);
 }
@@ -274,6 +276,7 @@ f3r_status f3r_default_params(f3r_params *p) {
     p->max_outer = 300;
     p->use_graphs = 1;
     p->keep_omega = 0;
+    p->fuse_cgs = 1;
     return F3R_OK;
 }
 
@@ -342,6 +345,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     }
     h->owns_stream = true;
     cudaStream_t s = h->cs;
+    c.zstream = s;
     cudaStream_t us = (cudaStream_t)stream;
     cudaEventCreate(&c.ev0);
     cudaEventCreate(&c.ev1);
@@ -408,17 +412,22 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     c.c_ntr_base = (long long *)dalloc(c, sizeof(long long));
     c.zst = dalloc(c, sizeof(double) * c.ld);
     c.apply_misc = dalloc(c, sizeof(double) * MS_COUNT);
-    const size_t pbytes = std::max((size_t)c.nsm * 8 * kMaxDots * sizeof(double),
-                                   (size_t)(kMaxOuterM + 2) * c.G1 * sizeof(double));
+    // partial sums: grid reductions, the outer CGS, and the fused kernels'
+    // [vector][block] regions (two of kMaxOuterM + 1 rows, one more row; <= 2 blocks per SM)
+    const size_t pbytes = std::max({(size_t)c.nsm * 8 * kMaxDots * sizeof(double),
+                                    (size_t)(kMaxOuterM + 2) * c.G1 * sizeof(double),
+                                    (size_t)(2 * (kMaxOuterM + 1) + 2) * c.nsm * 2 * sizeof(double)});
     c.partials = dalloc(c, pbytes);
     c.ticket = (unsigned *)dalloc(c, sizeof(unsigned) * 4);
+    c.coop = (unsigned *)dalloc(c, sizeof(unsigned) * 4);
     c.err = (int *)dalloc(c, sizeof(int) * 4);
     c.flags = (int *)dalloc(c, sizeof(int) * 16);
     c.jdev = (int *)dalloc(c, sizeof(int) * 4);
     h->rb_dev = (Readback *)dalloc(c, sizeof(Readback));
     if (!c.omega || !c.wcur || !c.counters || !c.c_ntr_base || !c.zst || !c.apply_misc || !c.partials ||
-        !c.ticket || !c.err || !c.flags || !c.jdev || !h->rb_dev)
+        !c.ticket || !c.coop || !c.err || !c.flags || !c.jdev || !h->rb_dev)
         return fail(F3R_ERR_NOMEM);
+    plan_cgs_fused(c);
     if (cudaHostAlloc((void **)&c.rb, sizeof(Readback), cudaHostAllocDefault) != cudaSuccess ||
         cudaHostAlloc((void **)&c.hostval, sizeof(double) * 8, cudaHostAllocDefault) != cudaSuccess)
         return fail(F3R_ERR_NOMEM);
@@ -469,6 +478,9 @@ f3r_status f3r_solve(f3r_ctx *h, const double *b, double *x, f3r_stats *stats, v
     cudaMemsetAsync(c.counters, 0, sizeof(unsigned long long) * 4, s);
     cudaMemsetAsync(c.flags, 0, sizeof(int) * 16, s);
     cudaMemsetAsync(c.err, 0, sizeof(int) * 4, s);
+    // reduction tickets and barrier counters: zero unless an earlier solve gave up inside a kernel
+    cudaMemsetAsync(c.ticket, 0, sizeof(unsigned) * 4, s);
+    cudaMemsetAsync(c.coop, 0, sizeof(unsigned) * 4, s);
     const long long launches0 = c.launches, glaunch0 = c.graph_launches;
 
     int hist_len = 0, true_len = 0;
@@ -649,7 +661,7 @@ int f3r_profile_slots(void) { return kProfSlots; }
 const char *f3r_profile_slot_name(int slot) {
     static const char *names[PK_KINDS] = {"spmv_dots", "cgs_pass", "cgs_final", "normalize", "combine",
                                           "level_start", "apply_M", "rich_fused2", "rich_step", "rich_update",
-                                          "outer_spmv", "outer_cgs", "outer_other", "spmv"};
+                                          "outer_spmv", "outer_cgs", "outer_other", "spmv", "cgs_fused"};
     if (slot < 0 || slot >= kProfSlots) return "";
     return names[slot / 4];
 }

@@ -35,15 +35,29 @@ __device__ __forceinline__ int2 tile_range(const Sell &A) {
     return make_int2(min(b, ntiles), min(b + per, ntiles));
 }
 
-// one row of a staged slice: sum_k a_k x(c_k) in CSR order
+// one row of a staged slice: sum_k a_k x(c_k) in CSR order.  Entries go in
+// groups of kRowGroup: all gathers of a group are issued before its first
+// fused multiply-add, so a row of up to kRowGroup entries waits for one
+// round of gather latency, not one per entry (the accumulation order is
+// unchanged).
+constexpr int kRowGroup = 8;
 template <class TC, class TA, class GX>
 __device__ __forceinline__ TC staged_row(const StageView<TA> &v, int lane, GX gx) {
     TC acc = (TC)0;
-#pragma unroll 8
-    for (int k = 0; k < v.w; ++k) {
-        const int c = v.col[k * kSlice + lane];
-        const TA a = v.val[k * kSlice + lane];
-        if (c >= 0) acc = fma_rn(to_c<TC>(a), gx(c), acc);
+    for (int k0 = 0; k0 < v.w; k0 += kRowGroup) {
+        int c[kRowGroup];
+        TC a[kRowGroup], xv[kRowGroup];
+#pragma unroll
+        for (int q = 0; q < kRowGroup; ++q) {
+            const int k = k0 + q;
+            c[q] = (k < v.w) ? v.col[k * kSlice + lane] : -1;
+            a[q] = (k < v.w) ? to_c<TC>(v.val[k * kSlice + lane]) : (TC)0;
+        }
+#pragma unroll
+        for (int q = 0; q < kRowGroup; ++q) xv[q] = (c[q] >= 0) ? gx(c[q]) : (TC)0;
+#pragma unroll
+        for (int q = 0; q < kRowGroup; ++q)
+            if (c[q] >= 0) acc = fma_rn(a[q], xv[q], acc);
     }
     return acc;
 }

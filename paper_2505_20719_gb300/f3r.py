@@ -34,7 +34,8 @@ class Params(C.Structure):
         ("rich_m", C.c_int), ("rich_a_prec", C.c_int), ("rich_v_prec", C.c_int), ("m_prec", C.c_int),
         ("precond", C.c_int), ("c", C.c_int), ("omega_fixed", C.c_double), ("diag_scale", C.c_int),
         ("row_scale", C.c_int), ("scale_cast", C.c_int), ("cgs_passes", C.c_int), ("tol", C.c_double),
-        ("max_outer", C.c_int), ("use_graphs", C.c_int), ("keep_omega", C.c_int), ("reserved", C.c_int * 7),
+        ("max_outer", C.c_int), ("use_graphs", C.c_int), ("keep_omega", C.c_int), ("fuse_cgs", C.c_int),
+        ("reserved", C.c_int * 6),
     ]
 
 

@@ -180,14 +180,16 @@ def test_richardson_update_call(convdiff, kind):
 
 
 # ------------------------------------------------------------ inner levels
+@pytest.mark.parametrize("fuse", [1, 0])
 @pytest.mark.parametrize("kind", ["fp16", "bf16", "fp32", "fp64"])
 @pytest.mark.parametrize("level", [1, 2])
-def test_inner_level_call(convdiff, kind, level):
-    """One call of F_{m2} (level 1) or F_{m3} (level 2) against the oracle."""
+def test_inner_level_call(convdiff, kind, level, fuse):
+    """One call of F_{m2} (level 1) or F_{m3} (level 2) against the oracle,
+    with the fused cooperative CGS2 / normalisation kernel and without."""
     prob = convdiff
     n = prob.n
     rs = 1 if kind == "bf16" else 0
-    s = solver(prob, _rich_prm(kind))
+    s = solver(prob, _rich_prm(kind, fuse_cgs=fuse))
     P = O.Problem(prob, diag_scale=1, row_scale=rs)
     is64 = kind == "fp64"
     v = rng.normal(11, 1, n)
@@ -321,6 +323,23 @@ def test_invalid_matrix_rejected():
     with pytest.raises(f3r.F3RError) as e:
         f3r.Solver(prob.rowptr, bad, prob.val, f3r.default_params())
     assert e.value.code == f3r.ERR_ARG
+
+
+@pytest.mark.parametrize("kind", ["fp16", "fp64"])
+def test_fused_and_unfused_cgs_agree(kind):
+    """The fused CGS2 / normalisation launch changes only the summation order
+    of the dot products: both paths converge alike and match the oracle."""
+    prob = G.diffusion3d_7pt(dims=(40, 36, 30), seed=108)
+    out = {}
+    for fuse in (0, 1):
+        s = solver(prob, _rich_prm(kind, fuse_cgs=fuse))
+        x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        out[fuse] = (s.solve(dev(prob.b), x), x.cpu().numpy())
+    P = O.Problem(prob, diag_scale=1)
+    ref = P.solve(_orc_prm(kind), prob.b)
+    for fuse in (0, 1):
+        _check_history(out[fuse][0], ref, prob, out[fuse][1])
+    assert abs(out[0][0].outer_iters - out[1][0].outer_iters) <= 1
 
 
 def test_graphs_and_direct_launches_agree():
