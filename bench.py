@@ -37,6 +37,8 @@ WORKLOADS = {
     "batched64": "64 uneven 2-D/3-D diffusion systems (n log-uniform in [1e4, 5e5]), 1-8 right-hand sides each",
     "learned27": "learned message-passing M vs Jacobi inside fp16-F3R: trained on the 100^3 27-point nodal "
                  "diffusion system, evaluated on 160^3 (log-normal nodal field, sigma 1.5)",
+    "sweep": "parameter and depth sweep of Sec. 6 (m2, m3, m4, c, fixed vs adaptive weight, depth variants "
+             "F3/F4 of Table 4) on the 128^3 7-point diffusion system",
 }
 
 
@@ -289,6 +291,8 @@ def run_learned(args):
     s64.close()
     st = f3r.Solver(T(tr.rowptr), T(tr.colidx), T(tr.val), f3r.default_params(precond=f3r.PC_LEARNED))
     st.learned_load(LI.flatten(LI.init_params(readout_scale=0.0)).astype(np.float32), train=True)
+    kind = {"error": 0, "residual": 1}[args.learned_loss]
+    st.learned_set_loss(kind)
     loss0, _ = st.learned_loss_grad(R, E)
     steps = 400
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -303,6 +307,20 @@ def run_learned(args):
     del R, E
     ev = G.by_name("diffusion27_160")
     b = T(ev.b)
+    # quality of one application on the evaluation matrix: ||r - A16 M r|| / ||r||
+    # for seeded normal r, with the trained net and with Jacobi
+    sq = f3r.Solver(T(ev.rowptr), T(ev.colidx), T(ev.val), f3r.default_params(precond=f3r.PC_LEARNED))
+    sq.learned_load(theta)
+    quality = {"learned": [], "jacobi": []}
+    for k in range(3):
+        r = T(rng.normal(950 + k, 7, ev.n)).float()
+        z = torch.empty_like(r)
+        u = torch.empty_like(r)
+        sq.learned_apply(r, z)
+        for name, zz in (("learned", z), ("jacobi", r)):
+            sq.spmv(f3r.F16, f3r.F32, zz, u)
+            quality[name].append(float((r - u).norm() / r.norm()))
+    sq.close()
     out = {}
     for name, prm in (("jacobi", f3r.default_params()), ("learned", f3r.default_params(precond=f3r.PC_LEARNED))):
         s = f3r.Solver(T(ev.rowptr), T(ev.colidx), T(ev.val), prm)
@@ -326,12 +344,68 @@ def run_learned(args):
            "value": out["learned"]["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": 1,
            "higher_is_better": False, "data": "synthetic",
            "config": {"workload": "learned27", "desc": WORKLOADS["learned27"], "train_n": n, "eval_n": ev.n,
-                      "eval_nnz": ev.nnz, "pairs": npairs, "train_steps": steps, "batch": 4, "lr": 2e-3},
+                      "eval_nnz": ev.nnz, "pairs": npairs, "train_steps": steps, "batch": 4, "lr": 2e-3,
+                      "loss": args.learned_loss},
            "learned": out["learned"], "jacobi": out["jacobi"],
            "speedup_vs_jacobi": out["jacobi"]["ms"] / out["learned"]["ms"],
-           "train": {"loss_initial": loss0, "loss_final": loss1, "loss_hist_first_last": [float(hist[0]), float(hist[-1])],
+           "apply_quality": quality,
+           "train": {"loss": args.learned_loss, "loss_initial": loss0, "loss_final": loss1, "loss_hist_first_last": [float(hist[0]), float(hist[-1])],
                      "train_ms": t_train, "pairs_s": t_pairs}}
     print(json.dumps(res))
+    return 0
+
+
+def run_sweep(args):
+    """Sec. 6 on one synthetic system: every configuration solved to 1e-9 from
+    x0 = 0 (one warm-up solve, then the median of --steps timed solves)."""
+    import torch
+    from paper_2505_20719_gb300 import f3r
+    from problems import generators as G
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    prob = G.by_name("diffusion7_128")
+    rp, ci, va, b = T(prob.rowptr), T(prob.colidx), T(prob.val), T(prob.b)
+    base = {"m": [100, 8, 4, 0]}
+    cases = [("default (100,8,4,2) c=64", "fp16-F3R", {})]
+    cases += [(f"m2={m2}", "fp16-F3R", {"m": [100, m2, 4, 0]}) for m2 in (4, 12, 15)]
+    cases += [(f"m3={m3}", "fp16-F3R", {"m": [100, 8, m3, 0]}) for m3 in (2, 3, 6, 8)]
+    cases += [(f"m4={m4}", "fp16-F3R", {"rich_m": m4}) for m4 in (1, 3, 4)]
+    cases += [(f"c={cc}", "fp16-F3R", {"c": cc}) for cc in (1, 16, 256)]
+    cases += [(f"fixed omega={w}", "fp16-F3R", {"omega_fixed": w}) for w in (0.8, 1.0, 1.3)]
+    cases += [(f"adaptive m3<=8 rtol={t}", "fp16-F3R", {"m": [100, 8, 8, 0], "inner_rtol": t})
+              for t in (0.4, 0.6, 0.8)]
+    cases += [("depth F3 (F100,F8,F8,M)", "F3", {}), ("depth F4 (F100,F8,F4,F2,M)", "F4", {}),
+              ("fp32-F3R", "fp32-F3R", {}), ("bf16-F3R", "bf16-F3R", {})]
+    del base
+    rows = []
+    for label, kind, kw in cases:
+        prm = f3r.preset(kind, **kw)
+        s = f3r.Solver(rp, ci, va, prm)
+        x = torch.zeros(prob.n, dtype=torch.float64, device=dev)
+        s.solve(b, x)
+        times = []
+        for _ in range(max(1, args.steps)):
+            x.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = s.solve(b, x)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        rows.append({"config": label, "solver": kind, "ms": statistics.median(times), "outer_iters": r.outer_iters,
+                     "m_applies": r.m_applies, "r_calls": r.r_calls, "status": f3r.STATUS.get(r.status),
+                     "rel_res": r.rel_res_true,
+                     "omega": [round(w, 4) for w in r.omega[:max(1, prm.rich_m)]]})
+        s.close()
+    ref = rows[0]["ms"]
+    for row in rows:
+        row["rel_time"] = row["ms"] / ref
+    out = {"metric": "Sec. 6 parameter / depth sweep: time-to-solution at 1e-9 per configuration", "value": ref,
+           "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": False,
+           "data": "synthetic", "config": {"workload": "sweep", "desc": WORKLOADS["sweep"], "n": prob.n,
+                                            "nnz": prob.nnz}, "rows": rows}
+    print(json.dumps(out))
     return 0
 
 
@@ -383,6 +457,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--fuse-cgs", type=int, default=1, choices=[0, 1],
                     help="1: CGS2 + normalisation of each inner iteration in one cooperative launch")
+    ap.add_argument("--learned-loss", default="residual", choices=["error", "residual"],
+                    help="training loss of --workload learned27")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -391,6 +467,8 @@ def main():
         return run_batched(args)
     if args.workload == "learned27":
         return run_learned(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
 
     import torch
     from paper_2505_20719_gb300 import f3r
@@ -466,11 +544,16 @@ def main():
     dom = max(prof, key=lambda k: prof[k]["ms"])
     n, nnz = prob.n, prob.nnz
     hbm, peak_src = _peaks()
-    # algorithmic bytes per launch of the candidate dominant kernels
+    # algorithmic bytes per launch of the candidate dominant kernels, for the
+    # storage read: int32 column index, A^ values asz bytes, row scales for bf16
+    isz = 4
+    asz = {"fp16-F3R": 2, "bf16-F3R": 2, "fp32-F3R": 4}.get(args.kind, 8)
+    vsz = {"fp16-F3R": 2, "bf16-F3R": 2, "fp32-F3R": 4}.get(args.kind, 8)
+    rsb = 4 * n if args.kind == "bf16-F3R" else 0
     algo = {
-        "rich_fused2_L0": 6 * nnz + 2 * n + 2 * n + 4 * n,   # A16 (val + int32 col), v16, m16, z fp32 out
-        "spmv_dots_L2": 6 * nnz + 4 * n + 4 * n + 4 * n * 2.5,  # A16, z fp32, w fp32 out, V[0..j] (avg 2.5)
-        "spmv_dots_L1": 8 * nnz + 4 * n + 4 * n + 4 * n * 4.5,  # A32, z, w, V[0..j] (avg 4.5)
+        "rich_fused2_L0": (isz + asz) * nnz + rsb + 2 * vsz * n + 4 * n,  # A, v, m, z (fp32) out
+        "spmv_dots_L2": (isz + asz) * nnz + rsb + 4 * n + 4 * n + 4 * n * 2.5,  # A, z, w out, V[0..j] (avg 2.5)
+        "spmv_dots_L1": (isz + 4) * nnz + 4 * n + 4 * n + 4 * n * 4.5,  # A32, z, w, V[0..j] (avg 4.5)
     }
     dk = dom if dom in algo else "rich_fused2_L0"
     avg_s = prof[dk]["avg_us"] * 1e-6
@@ -480,21 +563,22 @@ def main():
                 "algorithmic_bytes_per_launch": algo[dk], "avg_launch_us": prof[dk]["avg_us"],
                 "traffic": _ncu_traffic(dk)}
 
-    # ---- stand-alone fp16 SpMV (f3r_spmv), the metric's second half
+    # ---- stand-alone 16-bit SpMV (f3r_spmv), the metric's second half
+    sp_prec = {"fp16-F3R": f3r.F16, "bf16-F3R": f3r.BF16, "fp32-F3R": f3r.F32}.get(args.kind, f3r.F64)
     xs = torch.randn(n, device=dev, dtype=torch.float32)
     ys = torch.empty(n, device=dev, dtype=torch.float32)
     for _ in range(5):
-        s.spmv(f3r.F16, f3r.F32, xs, ys, stream=stream)
+        s.spmv(sp_prec, f3r.F32, xs, ys, stream=stream)
     reps = 50
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     flush.fill_(2.0)
     e0.record(stream)
     for _ in range(reps):
-        s.spmv(f3r.F16, f3r.F32, xs, ys, stream=stream)
+        s.spmv(sp_prec, f3r.F32, xs, ys, stream=stream)
     e1.record(stream)
     e1.synchronize()
     sp_us = e0.elapsed_time(e1) * 1e3 / reps
-    sp_bytes = 6 * nnz + 4 * n + 4 * n
+    sp_bytes = (isz + asz) * nnz + rsb + 4 * n + 4 * n
     spmv = {"achieved": sp_bytes / (sp_us * 1e-6) / 1e9, "avg_launch_us": sp_us, "unit": "GB/s",
             "algorithmic_bytes_per_launch": sp_bytes}
     spmv["frac"] = spmv["achieved"] / hbm
@@ -520,8 +604,23 @@ def main():
                                  "status": f3r.STATUS.get(rc.status), "rel_res": rc.rel_res_true}
             sc.close()
             del xc
+        # the paper's CG / BiCGStab comparators (fp64, same preconditioner)
+        for method in ("cg", "bicgstab"):
+            xc = torch.zeros(n, dtype=torch.float64, device=dev)
+            s.solve_krylov(method, b, xc, stream=stream)  # warm-up (graph capture)
+            xc.zero_()
+            flush.fill_(4.0)
+            e0.record(stream)
+            rc = s.solve_krylov(method, b, xc, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            comparators[method] = {"ms": e0.elapsed_time(e1), "iters": rc.outer_iters,
+                                   "status": f3r.STATUS.get(rc.status), "rel_res": rc.rel_res_true}
+            del xc
         comparators["speedup_vs_fgmres64"] = comparators["fgmres64"]["ms"] / ms_per_solve
         comparators["speedup_vs_fp32_f3r"] = comparators["fp32-F3R"]["ms"] / ms_per_solve
+        comparators["speedup_vs_cg"] = comparators["cg"]["ms"] / ms_per_solve
+        comparators["speedup_vs_bicgstab"] = comparators["bicgstab"]["ms"] / ms_per_solve
 
     # ---- end to end through the C ABI with host buffers (setup + solve + result)
     rp_h = torch.from_numpy(prob.rowptr).pin_memory()
@@ -550,7 +649,8 @@ def main():
         "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": WORKLOADS[args.workload], "solver": args.kind,
                    "n": n, "nnz": nnz, "tol": 1e-9, "parallelism": "replicas" if ws > 1 else "1 gpu",
-                   "l2": "flushed (256 MiB write) before every timed solve"},
+                   "l2": "flushed (256 MiB write) before every timed solve",
+                   "fuse_cgs": args.fuse_cgs},
         "outer_iters": last.outer_iters, "rel_res_true": true_rel, "status": f3r.STATUS.get(last.status),
         "roofline": roofline, "spmv_fp16": spmv, "kernels": prof, "comparators": comparators,
         "level_errors": level_errors, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,

@@ -82,7 +82,11 @@ typedef struct {
                            iteration in one cooperative launch (when a block's rows fit in
                            shared memory); 0: three launches.  Same arithmetic per row; only
                            the summation order of the dot products differs. */
-    int reserved[6];
+    float inner_rtol;   /* > 0: the innermost FGMRES level (F_m3 in F3R) stops once its
+                           residual estimate |g_{j+1}| <= inner_rtol * beta (adaptive m3,
+                           Sec. 6 / Sec. 7; the Richardson weight counter still counts the
+                           scheduled calls); 0: always m iterations */
+    int reserved[5];
 } f3r_params;
 
 typedef struct {
@@ -187,9 +191,14 @@ f3r_status f3r_learned_load(f3r_ctx *ctx, const float *params, int train);
 f3r_status f3r_learned_get(f3r_ctx *ctx, float *out);
 /* z = M_theta(r), r and z device fp32 vectors of n values. */
 f3r_status f3r_learned_apply(f3r_ctx *ctx, const float *r, float *z, void *stream);
-/* Mean loss over P samples of ||M_theta(r_p) - e_p||^2 / ||e_p||^2 and its
- * gradient (R, E device fp32, P x n row-major); loss and grad (NPARAMS) are
- * host outputs, either may be NULL. */
+/* Training loss: kind 0 (default) ||M_theta(r) - e||^2 / ||e||^2 with
+ * e = A^-1 r given; kind 1 ||A16 M_theta(r) - r||^2 / ||r||^2 with A16 the
+ * fp16 copy of A^ (no e needed: pass E = NULL).  Needs a loaded net;
+ * F3R_ERR_ARG for another kind. */
+f3r_status f3r_learned_set_loss(f3r_ctx *ctx, int kind);
+/* Mean loss over P samples (kind of f3r_learned_set_loss) and its gradient
+ * (R, E device fp32, P x n row-major; E may be NULL for kind 1); loss and
+ * grad (NPARAMS) are host outputs, either may be NULL. */
 f3r_status f3r_learned_loss_grad(f3r_ctx *ctx, const float *R, const float *E, int P, float *loss, float *grad,
                                  void *stream);
 /* Adam training: `steps` steps, each on a mini-batch of `batch` consecutive
@@ -197,6 +206,23 @@ f3r_status f3r_learned_loss_grad(f3r_ctx *ctx, const float *R, const float *E, i
  * optional, `steps` floats) receives each step's mini-batch loss. */
 f3r_status f3r_learned_train(f3r_ctx *ctx, const float *R, const float *E, int P, int steps, int batch, float lr,
                              float *loss_hist, void *stream);
+
+/* ------------------------------------------------------ Krylov comparators
+ * The paper's comparators (Sec. 5): preconditioned CG (symmetric A) and
+ * BiCGStab (any A), fp64 throughout, on the context's original matrix with
+ * the preconditioner the F3R nest wraps, P = D^-1/2 M D^-1/2 (M the stored
+ * Jacobi preconditioner in m_prec, D = |diag A| with diag_scale, else I).
+ * Stops when the recurrence residual falls below params.tol * ||b|| and the
+ * true fp64 residual confirms it (else the recurrence restarts from x, at
+ * most 3 times), or after max_iters iterations.  b, x: host or device fp64
+ * (x = x0 on entry).  stats: outer_iters = iterations, restarts, hist = the
+ * recurrence's ||r|| / ||b|| per iteration of the last start, rel_res_true;
+ * status F3R_ERR_BREAKDOWN when the method broke down (a zero inner product)
+ * before convergence. */
+#define F3R_KRYLOV_CG 1
+#define F3R_KRYLOV_BICGSTAB 2
+f3r_status f3r_solve_krylov(f3r_ctx *ctx, int method, const double *b, double *x, int max_iters,
+                            f3r_stats *stats, void *stream);
 
 /* ---------------------------------------------------------------- batched
  * Many systems, each with one or more right-hand sides, solved by F3R in a

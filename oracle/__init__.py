@@ -26,7 +26,7 @@ class Params(C.Structure):
         ("rich_m", C.c_int), ("rich_a_prec", C.c_int), ("rich_v_prec", C.c_int), ("m_prec", C.c_int),
         ("precond", C.c_int), ("c", C.c_int), ("omega_fixed", C.c_double), ("diag_scale", C.c_int),
         ("row_scale", C.c_int), ("scale_cast", C.c_int), ("cgs_passes", C.c_int), ("tol", C.c_double),
-        ("max_outer", C.c_int),
+        ("max_outer", C.c_int), ("inner_rtol", C.c_double),
     ]
 
 

@@ -427,20 +427,34 @@ struct Nest {
             for (int i = 0; i < n; ++i) z[i] = (T)(P.d[i] * (double)z[i]);
     }
 
+    /* Richardson calls that one child call of level d schedules. */
+    int64_t calls_below(int d) const {
+        if (d + 1 >= prm.nlevels) return prm.rich_m > 0 ? 1 : 0;
+        return (int64_t)prm.m[d + 1] * calls_below(d + 1);
+    }
+
     /* One call of an inner FGMRES level (x0 = 0, a fixed m iterations, no
-     * convergence check -- Sec. 4.2). */
+     * convergence check -- Sec. 4.2), or, with inner_rtol > 0 at the innermost
+     * FGMRES level, until its residual estimate falls below inner_rtol * beta.
+     * The weight counter c_ntr counts the scheduled Richardson calls: those of
+     * iterations a level does not run are added when it ends. */
     template <class T>
     void fgmres_inner(int d, const T *v, T *z) {
         const int n = P.n, m = prm.m[d];
         T beta = std::sqrt(dot_t(v, v, n));
         if (!std::isfinite(beta)) {
             for (int i = 0; i < n; ++i) z[i] = (T)NAN;
+            st->c_ntr += (int64_t)m * calls_below(d);
             return;
         }
         if (!(beta > 0)) {
             for (int i = 0; i < n; ++i) z[i] = 0;
+            st->c_ntr += (int64_t)m * calls_below(d);
             return;
         }
+        const bool adaptive = prm.inner_rtol > 0.0 && d == prm.nlevels - 1;
+        const T rtol = (T)prm.inner_rtol;
+        int ran = 0;
         std::vector<std::vector<T>> V(m + 1, std::vector<T>(n)), Z(m, std::vector<T>(n));
         std::vector<T> w(n), hcol(m + 1);
         Givens<T> G(m);
@@ -450,6 +464,7 @@ struct Nest {
         int kdim = 0;
         for (int j = 0; j < m; ++j) {
             apply_below<T>(d, V[j].data(), Z[j].data());
+            ran = j + 1;
             spmv_t<T>(P, prm.a_prec[d], Z[j].data(), w.data());
             cgs<T>(V, j, w, prm.cgs_passes, hcol);
             T hn = std::sqrt(dot_t(w.data(), w.data(), n));
@@ -457,9 +472,11 @@ struct Nest {
             if (!G.add_column(j, hcol, hn)) break;
             kdim = j + 1;
             if (!(hn > 0)) break;  // exact breakdown: the subspace holds the solution
+            if (adaptive && std::abs(G.g[j + 1]) <= rtol * beta) break;  // level residual small enough
             T invh = (T)1 / hn;
             for (int i = 0; i < n; ++i) V[j + 1][i] = w[i] * invh;
         }
+        st->c_ntr += (int64_t)(m - ran) * calls_below(d);
         std::vector<T> y = G.solve(kdim);
         combine(Z, y, kdim, z, n);
     }
@@ -606,6 +623,7 @@ void orc_default_params(orc_params *prm) {
     prm->cgs_passes = 2;
     prm->tol = 1e-9;
     prm->max_outer = 300;
+    prm->inner_rtol = 0.0;
 }
 
 void orc_spmv(void *p, int a_prec, int v_prec, const double *x, double *y) {

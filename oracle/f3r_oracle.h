@@ -42,6 +42,9 @@ typedef struct {
     int cgs_passes;     /* 1 = classical Gram-Schmidt, 2 = CGS2 */
     double tol;         /* relative residual target of the outer solver */
     int max_outer;      /* total outer iterations before giving up */
+    double inner_rtol;  /* > 0: the innermost FGMRES level stops once its residual estimate
+                           |g_{j+1}| <= inner_rtol * beta (adaptive m, Sec. 6 / Sec. 7);
+                           0: always m iterations */
 } orc_params;
 
 typedef struct {

@@ -14,6 +14,11 @@ The s-normalisation makes M_theta(a r) = a M_theta(r) for every power of two
 a > 0, and with wo = 0, omega_j = 1 it is the Jacobi preconditioner of A^
 (diag A^ = 1).
 
+Two training losses over samples p = 1..P (means over p):
+    error     ||M_theta(r_p) - e_p||^2 / ||e_p||^2        (e_p = A^-1 r_p)
+    residual  ||A M_theta(r_p) - r_p||^2 / ||r_p||^2      (A the matrix the
+              preconditioned level applies, here the fp16 copy of A^)
+
 forward() / backward() are plain fp64 numpy; forward(..., bf16=True) rounds
 the weights, the stored activations and the aggregated messages to bfloat16
 (the storage formats of the CUDA kernels) to give the reference the GPU is
@@ -115,5 +120,21 @@ def loss_and_grad(A_off, p, R, E):
         d = z - E[k]
         total += float(d @ d) / den / P
         gk = backward(A_off, p, cache, 2.0 * d / den / P)
+        grads = gk if grads is None else {key: grads[key] + gk[key] for key in grads}
+    return total, grads
+
+
+def loss_and_grad_residual(A, A_off, p, R):
+    """Mean over samples of ||A M_theta(r) - r||^2 / ||r||^2 and its gradient
+    (A: the full matrix, A_off: its off-diagonal graph for the net)."""
+    P = R.shape[0]
+    total = 0.0
+    grads = None
+    for k in range(P):
+        z, cache = forward(A_off, R[k], p)
+        den = float(R[k] @ R[k])
+        t = A @ z - R[k]
+        total += float(t @ t) / den / P
+        gk = backward(A_off, p, cache, 2.0 * (A.T @ t) / den / P)
         grads = gk if grads is None else {key: grads[key] + gk[key] for key in grads}
     return total, grads

@@ -722,7 +722,7 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
     // the batched path runs the default F3R precision schedule
     if (prm.nlevels != 3 || prm.rich_m != 2 || prm.a_prec[1] != F3R_F32 || prm.a_prec[2] != F3R_F16 ||
         prm.v_prec[1] != F3R_F32 || prm.v_prec[2] != F3R_F32 || prm.rich_a_prec != F3R_F16 ||
-        prm.rich_v_prec != F3R_F16 || prm.m_prec != F3R_F16 || prm.row_scale)
+        prm.rich_v_prec != F3R_F16 || prm.m_prec != F3R_F16 || prm.row_scale || prm.inner_rtol != 0.0f)
         return F3R_ERR_UNSUPPORTED;
     if (prm.m[0] < 1 || prm.m[0] > kMaxOuterM || prm.m[1] < 1 || prm.m[1] > kMaxInnerM || prm.m[2] < 1 ||
         prm.m[2] > kMaxInnerM || prm.c < 1 || prm.max_outer < 1 || (prm.cgs_passes != 1 && prm.cgs_passes != 2))

@@ -109,6 +109,7 @@ struct Ctx {
     double prof_ms[kProfSlots] = {};
     long long prof_cnt[kProfSlots] = {};
     LearnedState *learned = nullptr;  // learned preconditioner (precond = F3R_PC_LEARNED)
+    void *krylov = nullptr;           // CG / BiCGStab comparator state (krylov.cu)
 };
 
 inline void prof_begin(Ctx &c, int kind, int level, cudaStream_t s) {
@@ -175,9 +176,16 @@ f3r_status learned_loss_grad(Ctx &c, const float *R, const float *E, int P, cuda
 void learned_adam(Ctx &c, float lr, cudaStream_t s);
 void learned_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s);
 void learned_free(Ctx &c);
+f3r_status learned_set_loss(Ctx &c, int kind);
+int learned_loss_kind(const Ctx &c);
 float *learned_theta(Ctx &c);
 float *learned_grad(Ctx &c);
 float *learned_loss(Ctx &c);
+
+// krylov.cu: CG (method 1) / BiCGStab (method 2) on the original fp64 A
+f3r_status krylov_solve(Ctx &c, cudaStream_t s, int method, const double *b, double *x, int max_iters,
+                        f3r_stats *stats);
+void krylov_free(Ctx &c);
 
 // sizes
 int prec_bytes(int p);

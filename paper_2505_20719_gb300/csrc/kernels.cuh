@@ -38,6 +38,7 @@ __host__ __device__ inline int scal_size(int m) { return scal_misc(m) + MS_COUNT
 // Device view of one FGMRES level with vector type T.
 template <class T> struct LevelDev {
     int n, ld, m, depth;
+    float rtol;        // > 0: stop once |g_{j+1}| <= rtol * beta (adaptive inner level)
     T *V, *Z, *w;
     T *scal;
     int *flags;        // base of all levels' flags; this level's at flags[4*depth]
@@ -98,6 +99,7 @@ __device__ void givens_column(const LevelDev<T> &L, int j, const T *hcol, T hn, 
         fl[IF_KDIM] = j + 1;
         if (!(hn > (T)0)) stop = true;  // exact breakdown
         else L.misc()[MS_INV] = div_rn((T)1, hn);
+        if (L.rtol > 0.0f && fabs(g[j + 1]) <= mul_rn((T)L.rtol, L.misc()[MS_BETA])) stop = true;
     }
     if (stop) fl[IF_STOP] = 1;
     if (stop || last_iter) {

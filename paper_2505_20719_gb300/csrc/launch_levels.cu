@@ -12,6 +12,7 @@ template <class T> static LevelDev<T> levdev(Ctx &c, int d) {
     L.ld = c.ld;
     L.m = c.L[d].m;
     L.depth = d;
+    L.rtol = (d >= 1 && d == c.prm.nlevels - 1) ? c.prm.inner_rtol : 0.0f;
     L.V = (T *)c.L[d].V;
     L.Z = (T *)c.L[d].Z;
     L.w = (T *)c.L[d].w;

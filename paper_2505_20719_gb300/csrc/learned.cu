@@ -233,9 +233,11 @@ __device__ __forceinline__ void block_vec_sum(float (&v)[K], float *smem /* kLB/
 
 // dy = s coef (z - e); dP_L = bf16((wo dy) * [h_L > 0]); per-block partials
 // of [dwo (W) | domega_j | loss] in part[block][W + 2].
+// With gdir (residual loss) dy = s coef gdir and the loss term is lossv^2.
 __global__ void __launch_bounds__(kLB) k_lm_out_bwd(const float *z, const float *e, const float *r, int n,
                                                     const float *misc, const float *coef, NetDev net,
-                                                    const b16 *HL, b16 *dP, float *part) {
+                                                    const b16 *HL, b16 *dP, float *part, const float *gdir,
+                                                    const float *lossv) {
     pdl_enter();
     __shared__ float sm[(kLB / 32) * (W + 2)];
     const float s = misc[0], inv_s = misc[1], cf = *coef;
@@ -243,11 +245,12 @@ __global__ void __launch_bounds__(kLB) k_lm_out_bwd(const float *z, const float 
 #pragma unroll
     for (int k = 0; k < W + 2; ++k) acc[k] = 0.0f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float dif = sub_rn(z[i], e[i]);
+        const float dif = gdir ? gdir[i] : sub_rn(z[i], e[i]);
+        const float lt = gdir ? lossv[i] : dif;
         const float dy = mul_rn(mul_rn(s, cf), dif);
         const float rt = mul_rn(r[i], inv_s);
         acc[W] = fma_rn(rt, dy, acc[W]);
-        acc[W + 1] = fma_rn(mul_rn(0.5f, cf), mul_rn(dif, dif), acc[W + 1]);
+        acc[W + 1] = fma_rn(mul_rn(0.5f, cf), mul_rn(lt, lt), acc[W + 1]);
 #pragma unroll
         for (int ch = 0; ch < W / 8; ++ch) {
             const Pack<b16, 8> h = ldp<b16, 8>(HL + (size_t)i * W + ch * 8);
@@ -472,6 +475,12 @@ __global__ void k_lm_reduce(const float *part, int nblocks, int K, int map, int 
     }
 }
 
+// t = u - r (the residual of the net's output, u = A^ z)
+__global__ void __launch_bounds__(kBlock) k_lm_sub(const float *u, const float *r, float *t, int n) {
+    pdl_enter();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) t[i] = sub_rn(u[i], r[i]);
+}
+
 // 2 / (||e||^2 P) for the loss mean over P samples
 __global__ void __launch_bounds__(kBlock) k_lm_coef(const float *e, int n, int P, float *coef, GridRed<float> gr) {
     float acc[1] = {0.0f};
@@ -566,6 +575,8 @@ struct LearnedState {
     b16 *H[lm::NL + 1] = {}, *G[lm::NL] = {}, *dP[2] = {}, *U = nullptr;
     float *dHs = nullptr, *misc = nullptr, *part = nullptr, *coef = nullptr, *loss = nullptr, *zbuf = nullptr;
     float *r32 = nullptr;
+    float *tbuf = nullptr, *vbuf = nullptr;  // residual loss: A^ z - r and A^ (A^ z - r)
+    int loss_kind = 0;                       // 0: error loss, 1: residual loss
     int part_blocks = 0;
     bool train_buffers = false;
     int adam_step = 0;
@@ -620,6 +631,9 @@ f3r_status learned_enable(Ctx &c, const float *theta_host_or_dev, bool train) {
         L.dP[1] = (b16 *)lalloc(c, sizeof(b16) * hw);
         L.U = (b16 *)lalloc(c, sizeof(b16) * hw);
         L.dHs = (float *)lalloc(c, sizeof(float) * hw);
+        L.tbuf = (float *)lalloc(c, sizeof(float) * n);
+        L.vbuf = (float *)lalloc(c, sizeof(float) * n);
+        if (!L.tbuf || !L.vbuf) return F3R_ERR_NOMEM;
         for (int l = 2; l <= lm::NL; ++l)
             if (!L.H[l]) return F3R_ERR_NOMEM;
         for (int l = 0; l < lm::NL; ++l)
@@ -676,12 +690,26 @@ f3r_status learned_loss_grad(Ctx &c, const float *R, const float *E, int P, cuda
     cudaMemsetAsync(L.grad, 0, sizeof(float) * lm::kNP, s);
     cudaMemsetAsync(L.loss, 0, sizeof(float), s);
     for (int p = 0; p < P; ++p) {
-        const float *r = R + (size_t)p * n, *e = E + (size_t)p * n;
+        const float *r = R + (size_t)p * n, *e = E ? E + (size_t)p * n : nullptr;
         learned_forward(c, r, L.zbuf, true, s);
-        launch_pdl(lm::k_lm_coef, dim3(c.G), dim3(kBlock), 0, s, e, c.n, P, L.coef,
-                   GridRed<float>{(float *)c.partials, c.ticket, kMaxDots});
+        const float *gdir = nullptr, *lossv = nullptr;
+        if (L.loss_kind == 1) {
+            // residual loss: d/dz ||A^ z - r||^2 = 2 A^T (A^ z - r), A^ symmetric
+            launch_pdl(lm::k_lm_coef, dim3(c.G), dim3(kBlock), 0, s, r, c.n, P, L.coef,
+                       GridRed<float>{(float *)c.partials, c.ticket, kMaxDots});
+            if (launch_spmv(c, F3R_F16, F3R_F32, L.zbuf, L.vbuf, s) != F3R_OK) return F3R_ERR_UNSUPPORTED;
+            launch_pdl(lm::k_lm_sub, dim3(c.G), dim3(kBlock), 0, s, (const float *)L.vbuf, r, L.tbuf, c.n);
+            if (launch_spmv(c, F3R_F16, F3R_F32, L.tbuf, L.vbuf, s) != F3R_OK) return F3R_ERR_UNSUPPORTED;
+            gdir = L.vbuf;
+            lossv = L.tbuf;
+            c.launches += 2;
+        } else {
+            launch_pdl(lm::k_lm_coef, dim3(c.G), dim3(kBlock), 0, s, e, c.n, P, L.coef,
+                       GridRed<float>{(float *)c.partials, c.ticket, kMaxDots});
+        }
         launch_pdl(lm::k_lm_out_bwd, dim3(g), dim3(lm::kLB), 0, s, (const float *)L.zbuf, e, r, c.n,
-                   (const float *)L.misc, (const float *)L.coef, net, (const b16 *)L.H[lm::NL], L.dP[0], L.part);
+                   (const float *)L.misc, (const float *)L.coef, net, (const b16 *)L.H[lm::NL], L.dP[0], L.part,
+                   gdir, lossv);
         lm::k_lm_reduce<<<1, 64, 0, s>>>(L.part, g, lm::W + 2, 1, 0, L.grad, L.loss);
         int cur = 0;
         for (int l = lm::NL - 1; l >= 0; --l) {
@@ -749,6 +777,13 @@ void learned_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_
         c.launches += 2;
     }
 }
+
+f3r_status learned_set_loss(Ctx &c, int kind) {
+    if (!c.learned || (kind != 0 && kind != 1)) return F3R_ERR_ARG;
+    c.learned->loss_kind = kind;
+    return F3R_OK;
+}
+int learned_loss_kind(const Ctx &c) { return c.learned ? c.learned->loss_kind : 0; }
 
 float *learned_theta(Ctx &c) { return c.learned ? c.learned->theta : nullptr; }
 float *learned_grad(Ctx &c) { return c.learned ? c.learned->grad : nullptr; }

@@ -75,6 +75,7 @@ f3r_status check_params(const f3r_params &p) {
     }
     if (p.c < 1 || p.max_outer < 1 || !(p.tol >= 0.0)) return F3R_ERR_ARG;
     if (p.cgs_passes != 1 && p.cgs_passes != 2) return F3R_ERR_ARG;
+    if (!(p.inner_rtol >= 0.0f && p.inner_rtol < 1.0f)) return F3R_ERR_ARG;
     if (p.precond != F3R_PC_IDENTITY && p.precond != F3R_PC_JACOBI && p.precond != F3R_PC_LEARNED) return F3R_ERR_ARG;
     if (p.precond == F3R_PC_LEARNED &&
         (p.rich_m < 1 || p.rich_v_prec != F3R_F16 || p.rich_a_prec != F3R_F16 || p.row_scale))
@@ -300,6 +301,7 @@ void f3r_destroy(f3r_ctx *h) {
     Ctx &c = h->c;
     for (auto &kv : c.graphs) cudaGraphExecDestroy(kv.second);
     learned_free(c);
+    krylov_free(c);
     for (auto &r : c.prec) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -578,6 +580,49 @@ f3r_status f3r_solve(f3r_ctx *h, const double *b, double *x, f3r_stats *stats, v
     return status;
 }
 
+f3r_status f3r_solve_krylov(f3r_ctx *h, int method, const double *b, double *x, int max_iters, f3r_stats *stats,
+                            void *stream) {
+    if (!h || !b || !x || (method != F3R_KRYLOV_CG && method != F3R_KRYLOV_BICGSTAB) || max_iters < 0)
+        return F3R_ERR_ARG;
+    Ctx &c = h->c;
+    cudaStream_t s = h->cs;
+    cudaStream_t us = (cudaStream_t)stream;
+    const int n = c.n;
+    cudaEventRecord(c.ev0, us);
+    cudaStreamWaitEvent(s, c.ev0, 0);
+    const bool bdevp = is_device_ptr(b), xdevp = is_device_ptr(x);
+    const double *bd = b;
+    double *xd = x;
+    if (!bdevp || !xdevp) {
+        if (!c.bdev) {
+            c.bdev = (double *)dalloc(c, sizeof(double) * n);
+            c.xdev = (double *)dalloc(c, sizeof(double) * n);
+            if (!c.bdev || !c.xdev) return F3R_ERR_NOMEM;
+        }
+        if (!bdevp) {
+            cudaMemcpyAsync(c.bdev, b, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+            bd = c.bdev;
+        }
+        if (!xdevp) {
+            cudaMemcpyAsync(c.xdev, x, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+            xd = c.xdev;
+        }
+    }
+    cudaEventRecord(c.ev0, s);
+    f3r_status st = krylov_solve(c, s, method == F3R_KRYLOV_CG ? 1 : 2, bd, xd, max_iters, stats);
+    cudaEventRecord(c.ev1, s);
+    if (!xdevp) cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return F3R_ERR_CUDA;
+    if (stats) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+        stats->t_solve_ms = ms;
+    }
+    cudaEventRecord(c.ev1, s);
+    cudaStreamWaitEvent(us, c.ev1, 0);
+    return st;
+}
+
 f3r_status f3r_spmv(f3r_ctx *h, int p, int vp, const void *x, void *y, void *stream) {
     if (!h || !x || !y) return F3R_ERR_ARG;
     f3r_status st = launch_spmv(h->c, p, vp, x, y, (cudaStream_t)stream);
@@ -666,6 +711,11 @@ const char *f3r_profile_slot_name(int slot) {
     return names[slot / 4];
 }
 
+f3r_status f3r_learned_set_loss(f3r_ctx *h, int kind) {
+    if (!h) return F3R_ERR_ARG;
+    return learned_set_loss(h->c, kind);
+}
+
 f3r_status f3r_learned_load(f3r_ctx *h, const float *params, int train) {
     if (!h || !params) return F3R_ERR_ARG;
     return learned_enable(h->c, params, train != 0);
@@ -687,7 +737,8 @@ f3r_status f3r_learned_apply(f3r_ctx *h, const float *r, float *z, void *stream)
 
 f3r_status f3r_learned_loss_grad(f3r_ctx *h, const float *R, const float *E, int P, float *loss, float *grad,
                                  void *stream) {
-    if (!h || !R || !E || P < 1 || !h->c.learned) return F3R_ERR_ARG;
+    if (!h || !R || P < 1 || !h->c.learned) return F3R_ERR_ARG;
+    if (!E && learned_loss_kind(h->c) == 0) return F3R_ERR_ARG;
     f3r_status st = learned_enable(h->c, nullptr, true);
     if (st != F3R_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -701,7 +752,8 @@ f3r_status f3r_learned_loss_grad(f3r_ctx *h, const float *R, const float *E, int
 
 f3r_status f3r_learned_train(f3r_ctx *h, const float *R, const float *E, int P, int steps, int batch, float lr,
                              float *loss_hist, void *stream) {
-    if (!h || !R || !E || P < 1 || steps < 0 || batch < 1 || batch > P || !h->c.learned) return F3R_ERR_ARG;
+    if (!h || !R || P < 1 || steps < 0 || batch < 1 || batch > P || !h->c.learned) return F3R_ERR_ARG;
+    if (!E && learned_loss_kind(h->c) == 0) return F3R_ERR_ARG;
     f3r_status st = learned_enable(h->c, nullptr, true);
     if (st != F3R_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -709,7 +761,7 @@ f3r_status f3r_learned_train(f3r_ctx *h, const float *R, const float *E, int P, 
     int p0 = 0;
     for (int k = 0; k < steps; ++k) {
         const int b = std::min(batch, P - p0);
-        st = learned_loss_grad(h->c, R + (size_t)p0 * n, E + (size_t)p0 * n, b, s);
+        st = learned_loss_grad(h->c, R + (size_t)p0 * n, E ? E + (size_t)p0 * n : nullptr, b, s);
         if (st != F3R_OK) return st;
         learned_adam(h->c, lr, s);
         if (loss_hist) {

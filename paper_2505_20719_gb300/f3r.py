@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libf3r.so")
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
 PC_IDENTITY, PC_JACOBI, PC_LEARNED = 0, 1, 2
+KRYLOV_CG, KRYLOV_BICGSTAB = 1, 2
 LEARNED_NPARAMS = 6337
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "not converged",
           5: "breakdown", 6: "non-finite value", 7: "device wait timed out", 8: "unsupported"}
@@ -35,7 +36,7 @@ class Params(C.Structure):
         ("precond", C.c_int), ("c", C.c_int), ("omega_fixed", C.c_double), ("diag_scale", C.c_int),
         ("row_scale", C.c_int), ("scale_cast", C.c_int), ("cgs_passes", C.c_int), ("tol", C.c_double),
         ("max_outer", C.c_int), ("use_graphs", C.c_int), ("keep_omega", C.c_int), ("fuse_cgs", C.c_int),
-        ("reserved", C.c_int * 6),
+        ("inner_rtol", C.c_float), ("reserved", C.c_int * 5),
     ]
 
 
@@ -109,8 +110,11 @@ def lib():
         L.f3r_learned_apply.argtypes = [vp, vp, vp, vp]
         L.f3r_learned_loss_grad.argtypes = [vp, vp, vp, C.c_int, vp, vp, vp]
         L.f3r_learned_train.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, vp, vp]
+        L.f3r_learned_set_loss.argtypes = [vp, C.c_int]
+        L.f3r_solve_krylov.argtypes = [vp, C.c_int, vp, vp, C.c_int, C.POINTER(Stats), vp]
+        L.f3r_solve_krylov.restype = C.c_int
         for name in ("f3r_learned_load", "f3r_learned_get", "f3r_learned_apply", "f3r_learned_loss_grad",
-                     "f3r_learned_train"):
+                     "f3r_learned_train", "f3r_learned_set_loss"):
             getattr(L, name).restype = C.c_int
         L.f3r_residual_noalloc.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.f3r_residual_noalloc.restype = C.c_int
@@ -165,7 +169,8 @@ def default_params(**kw) -> Params:
 def preset(name: str, **kw) -> Params:
     """Named configurations: fp16-F3R (Table 1), bf16-F3R (bf16 inner storage
     with per-row scaling), fp32-F3R and fp64-F3R (Sec. 5), fgmres64 (fp64
-    restarted FGMRES(64) with M, Sec. 5)."""
+    restarted FGMRES(64) with M, Sec. 5), and the depth variants F3 and F4 of
+    Table 4."""
     if name == "fp16-F3R":
         p = default_params()
     elif name == "bf16-F3R":
@@ -178,6 +183,13 @@ def preset(name: str, **kw) -> Params:
                            rich_v_prec=F64, m_prec=F64)
     elif name == "fgmres64":
         p = default_params(nlevels=1, m=[64, 0, 0, 0], rich_m=0, m_prec=F64, max_outer=19200)
+    elif name == "F3":
+        # Table 4: (F100, F8, F8, M), the inner F8 with fp16 A and fp32 vectors
+        p = default_params(nlevels=3, m=[100, 8, 8, 0], rich_m=0, m_prec=F16)
+    elif name == "F4":
+        # Table 4: (F100, F8, F4, F2, M) with fp32 vectors in F2 (the GPU keeps
+        # inner FGMRES vectors in fp32)
+        p = default_params(nlevels=4, m=[100, 8, 4, 2], a_prec=[F64, F32, F16, F16], rich_m=0, m_prec=F16)
     else:
         raise KeyError(name)
     return _set(p, kw)
@@ -243,6 +255,23 @@ class Solver:
             raise F3RError(code, "f3r_solve")
         return Result(st, hist[:min(st.hist_len, hist_cap)].copy(), th[:min(st.true_len, 256)].copy())
 
+    def solve_krylov(self, method: str, b, x, max_iters: int = 100000, stream=None,
+                     hist_cap: int = 1 << 17) -> Result:
+        """The paper's comparators on this context's matrix: method 'cg' or
+        'bicgstab' (fp64, preconditioner D^-1/2 M D^-1/2)."""
+        m = {"cg": KRYLOV_CG, "bicgstab": KRYLOV_BICGSTAB}[method]
+        hist = np.zeros(hist_cap)
+        th = np.zeros(4)
+        st = Stats()
+        st.hist = hist.ctypes.data_as(C.POINTER(C.c_double))
+        st.hist_cap = hist_cap
+        st.true_hist = th.ctypes.data_as(C.POINTER(C.c_double))
+        st.true_cap = 4
+        code = lib().f3r_solve_krylov(self.h, m, _ptr(b), _ptr(x), int(max_iters), C.byref(st), _stream(stream))
+        if code not in (OK, NOT_CONVERGED, ERR_NONFINITE, ERR_BREAKDOWN):
+            raise F3RError(code, "f3r_solve_krylov")
+        return Result(st, hist[:min(st.hist_len, hist_cap)].copy(), th[:min(st.true_len, 4)].copy())
+
     def spmv(self, p: int, vp: int, x, y, stream=None):
         _check(lib().f3r_spmv(self.h, p, vp, _ptr(x), _ptr(y), _stream(stream)), "f3r_spmv")
 
@@ -293,6 +322,10 @@ class Solver:
 
     def learned_apply(self, r, z, stream=None):
         _check(lib().f3r_learned_apply(self.h, _ptr(r), _ptr(z), _stream(stream)), "f3r_learned_apply")
+
+    def learned_set_loss(self, kind: int):
+        """0: error loss ||M(r) - e||^2/||e||^2; 1: residual loss ||A16 M(r) - r||^2/||r||^2."""
+        _check(lib().f3r_learned_set_loss(self.h, int(kind)), "f3r_learned_set_loss")
 
     def learned_loss_grad(self, R, E, stream=None):
         """R, E: device fp32 (P, n).  Returns (loss, grad)."""

@@ -77,6 +77,31 @@ def test_gradient_matches_oracle(setup):
         assert np.linalg.norm(a - b) <= 0.15 * np.linalg.norm(b) + 1e-6, k
 
 
+def test_residual_loss_gradient_matches_oracle(setup):
+    """Residual loss ||A16 M(r) - r||^2 / ||r||^2 (no error vectors needed)."""
+    prob, s, A16 = setup
+    import scipy.sparse as sp
+    P = O.Problem(prob, diag_scale=1)
+    A16full = sp.csr_matrix((P.get("a16"), prob.colidx, prob.rowptr), shape=(prob.n, prob.n))
+    p = LI.init_params(readout_scale=0.5)
+    flat = LI.flatten(p).astype(np.float32)
+    s.learned_load(flat, train=True)
+    s.learned_set_loss(1)
+    try:
+        R = rng.normal(13, 7, 2 * prob.n).reshape(2, prob.n).astype(np.float32)
+        loss, grad = s.learned_loss_grad(dev(R), None)
+    finally:
+        s.learned_set_loss(0)
+    pf = LI.unflatten(flat.astype(np.float64))
+    want_loss, want = LM.loss_and_grad_residual(A16full, A16, pf, R.astype(np.float64))
+    assert abs(loss - want_loss) <= 2e-2 * want_loss
+    g = LI.unflatten(grad.astype(np.float64))
+    for k in LI.PARAM_ORDER:
+        a, b = np.ravel(g[k]), np.ravel(want[k])
+        assert _cos(a, b) >= 0.99, k
+        assert np.linalg.norm(a - b) <= 0.15 * np.linalg.norm(b) + 1e-6, k
+
+
 def test_training_reduces_loss_and_solves(setup):
     prob, s, A16 = setup
     n = prob.n

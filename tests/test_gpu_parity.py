@@ -117,6 +117,25 @@ def test_spmv_full_size_bit_exact(which):
     assert np.array_equal(y.cpu().numpy().astype(np.float64), want)
 
 
+def test_spmv_and_solve_random_far_columns():
+    """A random sparse pattern (columns up to n away from their row, no
+    locality for the x gathers): SpMV bit-exact and the solve converges."""
+    prob = G.random_dd_sparse(70000, per_row=5, seed=109, dominance=1.5)
+    rows = np.repeat(np.arange(prob.n), np.diff(prob.rowptr))
+    assert np.max(np.abs(prob.colidx.astype(np.int64) - rows)) > 32767
+    s = solver(prob, f3r.default_params())
+    P = O.Problem(prob, diag_scale=1)
+    x = rng.normal(10, 1, prob.n).astype(np.float32)
+    y = torch.empty(prob.n, dtype=torch.float32, device="cuda")
+    s.spmv(f3r.F16, f3r.F32, dev(x), y)
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy().astype(np.float64), P.spmv(O.F16, O.F32, x.astype(np.float64)))
+    xs = np.zeros(prob.n)
+    res = s.solve(np.ascontiguousarray(prob.b), xs)
+    A = prob.to_scipy()
+    assert res.status == f3r.OK and np.linalg.norm(prob.b - A @ xs) / np.linalg.norm(prob.b) < 1e-9
+
+
 # ------------------------------------------------------------- Richardson
 def _rich_prm(kind, **kw):
     if kind == "fp16":
@@ -257,6 +276,35 @@ def test_solve_convdiff_matches_oracle(kind):
     prob = G.convdiff3d_27pt(dims=(20, 20, 20), seed=103)
     res, ref, xg = _solve_both(prob, kind)
     _check_history(res, ref, prob, xg)
+
+
+@pytest.mark.parametrize("name", ["F3", "F4"])
+def test_depth_variants_match_oracle(name):
+    """The depth variants of Table 4 (F3: (F100, F8, F8, M); F4: (F100, F8,
+    F4, F2, M)) against the oracle's same configurations."""
+    prob = G.diffusion3d_7pt(dims=(24, 24, 24), seed=102)
+    s = solver(prob, f3r.preset(name))
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    res = s.solve(dev(prob.b), x)
+    torch.cuda.synchronize()
+    ref = O.Problem(prob, diag_scale=1).solve(O.preset(name), prob.b)
+    _check_history(res, ref, prob, x.cpu().numpy())
+
+
+@pytest.mark.parametrize("fuse", [1, 0])
+def test_adaptive_inner_level_matches_oracle(fuse):
+    """Adaptive m3: F_m3 (up to 8 iterations) stops once its residual estimate
+    is below 0.2 beta; the weight counter follows the scheduled calls."""
+    prob = G.diffusion3d_7pt(dims=(24, 24, 24), seed=102)
+    kw = dict(m=[100, 8, 8, 0], inner_rtol=0.2)
+    s = solver(prob, f3r.default_params(fuse_cgs=fuse, **kw))
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    res = s.solve(dev(prob.b), x)
+    torch.cuda.synchronize()
+    ref = O.Problem(prob, diag_scale=1).solve(O.params(**kw), prob.b)
+    _check_history(res, ref, prob, x.cpu().numpy())
+    assert res.r_calls < 64 * res.outer_iters and res.m_applies == 2 * res.r_calls
+    assert abs(res.r_calls / res.outer_iters - ref.r_calls / ref.outer_iters) <= 0.1 * ref.r_calls / ref.outer_iters
 
 
 def test_fgmres64_comparator_matches_oracle():

@@ -35,6 +35,34 @@ def test_gradient_matches_central_differences():
         assert abs(fd - gflat[k]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (k, fd, gflat[k])
 
 
+def test_residual_loss_gradient_matches_central_differences():
+    """The residual loss ||A M(r) - r||^2 / ||r||^2: analytic gradient
+    against central differences, and its value by a direct evaluation."""
+    prob = G.diffusion27_nodal(dims=(4, 4, 4), seed=603)
+    P = O.Problem(prob, diag_scale=1)
+    import scipy.sparse as sp
+    Afull = sp.csr_matrix((P.get("ahat"), prob.colidx, prob.rowptr), shape=(prob.n, prob.n))
+    A = LM.offdiag(P.get("ahat"), prob.rowptr, prob.colidx, prob.n)
+    p = LI.init_params(readout_scale=0.3)
+    R = rng.normal(6, 1, 2 * prob.n).reshape(2, prob.n)
+    f0, g = LM.loss_and_grad_residual(Afull, A, p, R)
+    want = np.mean([np.sum((Afull @ LM.forward(A, R[k], p)[0] - R[k]) ** 2) / np.sum(R[k] ** 2) for k in range(2)])
+    assert abs(f0 - want) <= 1e-12 * want
+    flat = LI.flatten(p)
+    gflat = LI.flatten(g)
+    h = 1e-6
+    idx = np.concatenate([np.arange(0, 64), rng.integers(7, 1, 150, 64, flat.size - 1)])
+    for k in idx:
+        fp = flat.copy()
+        fp[k] += h
+        fm = flat.copy()
+        fm[k] -= h
+        lp, _ = LM.loss_and_grad_residual(Afull, A, LI.unflatten(fp), R)
+        lm, _ = LM.loss_and_grad_residual(Afull, A, LI.unflatten(fm), R)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gflat[k]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, (k, fd, gflat[k])
+
+
 def test_untrained_net_is_jacobi_and_scale_homogeneous():
     prob, A = _graph()
     p = LI.init_params(readout_scale=0.0)

@@ -332,6 +332,35 @@ def test_counting_invariant(orc):
     assert res.r_update_calls == (32 * res.outer_iters) // 64
 
 
+def test_adaptive_inner_level_reductions(orc):
+    """Adaptive m3 (Sec. 6 / Sec. 7, stop the innermost FGMRES level once
+    |g_{j+1}| <= rtol * beta): a threshold no estimate reaches is the fixed-m
+    solver exactly; a threshold every first step meets (|g_1| = |s_0| beta <
+    beta) is m3 = 1 exactly when the weights are fixed (the weight counter
+    then plays no part)."""
+    prob = G.diffusion3d_7pt(dims=(12, 11, 10), seed=23)
+    P = O.Problem(prob, diag_scale=1)
+    a = P.solve(O.params(inner_rtol=1e-300), prob.b)
+    b = P.solve(O.params(), prob.b)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.hist, b.hist) and a.r_calls == b.r_calls
+    c = P.solve(O.params(inner_rtol=1.0 - 2.0 ** -20, omega_fixed=1.0), prob.b)
+    d = P.solve(O.params(m=[100, 8, 1, 0], omega_fixed=1.0), prob.b)
+    assert np.array_equal(c.x, d.x) and np.array_equal(c.hist, d.hist)
+    assert c.r_calls == d.r_calls == 8 * c.outer_iters
+
+
+def test_adaptive_inner_level_counts(orc):
+    """With a moderate threshold the level runs fewer Richardson calls than it
+    schedules; every executed call still applies M m4 times, and the solve
+    converges."""
+    prob = G.diffusion3d_7pt(dims=(14, 14, 14), seed=24)
+    P = O.Problem(prob, diag_scale=1)
+    res = P.solve(O.params(m=[100, 8, 8, 0], inner_rtol=0.2), prob.b)
+    assert res.status == O.OK and res.rel_res_true < 1e-9
+    assert 8 * res.outer_iters <= res.r_calls < 64 * res.outer_iters
+    assert res.m_applies == 2 * res.r_calls
+
+
 def test_fp16_iterations_close_to_fp64(orc):
     """Sec. 5.1: fp16-F3R needs at most ~9 % more iterations than fp64-F3R."""
     for prob, ds in [(G.poisson2d_5pt(64), 0), (G.diffusion3d_7pt(dims=(20, 20, 20), seed=19), 1)]:
