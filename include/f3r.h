@@ -50,7 +50,7 @@ typedef enum {
 } f3r_status;
 
 enum { F3R_F64 = 0, F3R_F32 = 1, F3R_F16 = 2, F3R_BF16 = 3 };
-enum { F3R_PC_IDENTITY = 0, F3R_PC_JACOBI = 1, F3R_PC_LEARNED = 2 };
+enum { F3R_PC_IDENTITY = 0, F3R_PC_JACOBI = 1, F3R_PC_LEARNED = 2, F3R_PC_AINV = 3 };
 
 /* Solver configuration.  f3r_default_params gives F3R with the paper's
  * defaults: (m1, m2, m3, m4) = (100, 8, 4, 2), c = 64, Table 1 precisions,
@@ -65,9 +65,13 @@ typedef struct {
     int rich_a_prec;    /* precision of A inside Richardson */
     int rich_v_prec;    /* precision of Richardson vectors: F16, BF16, F32 or F64 */
     int m_prec;         /* storage precision of M */
-    int precond;        /* F3R_PC_JACOBI (M = diag(A^)^-1), F3R_PC_IDENTITY, or F3R_PC_LEARNED
+    int precond;        /* F3R_PC_JACOBI (M = diag(A^)^-1), F3R_PC_IDENTITY, F3R_PC_LEARNED
                            (the learned net as M inside an fp16 Richardson level; Jacobi
-                           until f3r_learned_load is called) */
+                           until f3r_learned_load is called), or F3R_PC_AINV: the
+                           two-SpMV approximate inverse
+                             M = (I - Dt^-1 U) Dt^-1 (I - L Dt^-1),  Dt = ainv_alpha diag(A^),
+                           L / U the strict triangles of A^, factors stored in fp16
+                           (fp16 Richardson level, no row scaling) */
     int c;              /* weight-update period of Algorithm 1 (>= 1) */
     double omega_fixed; /* > 0: fixed Richardson weight, no adaptive update */
     int diag_scale;     /* 1: inner nest works on A^ = D^-1/2 A D^-1/2, D = |diag A| (Sec. 5) */
@@ -86,7 +90,13 @@ typedef struct {
                            residual estimate |g_{j+1}| <= inner_rtol * beta (adaptive m3,
                            Sec. 6 / Sec. 7; the Richardson weight counter still counts the
                            scheduled calls); 0: always m iterations */
-    int reserved[5];
+    float ainv_alpha;   /* diagonal boost of the approximate inverse (> 0; default 1) */
+    int fuse_step;      /* 1 (with fuse_cgs): a plain iteration of the innermost FGMRES level
+                           (Richardson call, SpMV + dots, CGS2, normalisation) in one
+                           cooperative launch when the default precision schedule, Jacobi M
+                           and m4 = 2 apply; 0 (default): separate launches, which measured
+                           as fast inside CUDA graphs with more blocks per SM */
+    int reserved[3];
 } f3r_params;
 
 typedef struct {
@@ -155,7 +165,10 @@ f3r_status f3r_set_rich_state(f3r_ctx *ctx, const double *omega8, int64_t c_ntr)
 /* Copy a set-up array back to host memory `out` in CSR order (test entry):
  * 0 d = D^-1/2 (double, n); 1 A^ fp64 (nnz); 2 A^ fp32 (float, nnz);
  * 3 A^/s fp16 (uint16 bits, nnz); 4 A^/s bf16 (uint16 bits, nnz);
- * 5 row scales (float, n); 6 M in m_prec (n elements of that precision).
+ * 5 row scales (float, n); 6 M in m_prec (n elements of that precision);
+ * approximate inverse (F3R_PC_AINV), fp16 bits: 7 L Dt^-1 (nnz, zero off the
+ * strict lower triangle), 8 Dt^-1 U (nnz, zero off the strict upper
+ * triangle), 9 Dt^-1 (n).
  * Returns F3R_ERR_ARG if the array does not exist. */
 f3r_status f3r_export(f3r_ctx *ctx, int which, void *out);
 

@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
-PC_IDENTITY, PC_JACOBI = 0, 1
+PC_IDENTITY, PC_JACOBI, PC_AINV = 0, 1, 3
 OK, ERR_ARG, NOT_CONVERGED, BREAKDOWN, NONFINITE = 0, 1, 4, 5, 6
 
 
@@ -58,6 +58,7 @@ def lib():
         L.orc_problem_create.argtypes = [C.c_int32, ip, ip, dp, C.c_int, C.c_int, C.c_int]
         L.orc_problem_create.restype = C.c_void_p
         L.orc_problem_destroy.argtypes = [C.c_void_p]
+        L.orc_problem_set_ainv.argtypes = [C.c_void_p, C.c_double]
         L.orc_problem_get.argtypes = [C.c_void_p, C.c_int, dp]
         L.orc_problem_get.restype = C.c_int64
         L.orc_default_params.argtypes = [C.POINTER(Params)]
@@ -167,15 +168,18 @@ class Problem:
     """The oracle's copy of one matrix with its scaled and rounded variants."""
 
     WHICH = {"d": 0, "ahat": 1, "a32": 2, "a16": 3, "abf16": 4, "rs16": 5, "rsbf16": 6,
-             "m64": 7, "m32": 8, "m16": 9, "mbf16": 10}
+             "m64": 7, "m32": 8, "m16": 9, "mbf16": 10, "ainv_l": 11, "ainv_u": 12, "ainv_dinv": 13}
 
-    def __init__(self, prob, diag_scale=1, row_scale=0, precond=PC_JACOBI):
+    def __init__(self, prob, diag_scale=1, row_scale=0, precond=PC_JACOBI, ainv_alpha=1.0):
         self.n = prob.n
         self._rp = np.ascontiguousarray(prob.rowptr, dtype=np.int32)
         self._ci = np.ascontiguousarray(prob.colidx, dtype=np.int32)
         self._v = np.ascontiguousarray(prob.val, dtype=np.float64)
         self.h = lib().orc_problem_create(self.n, _ip(self._rp), _ip(self._ci), _dp(self._v),
                                           diag_scale, row_scale, precond)
+        if precond == PC_AINV:
+            # the boost is a single-precision parameter of the solver (f3r_params.ainv_alpha)
+            lib().orc_problem_set_ainv(self.h, float(np.float32(ainv_alpha)))
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -98,6 +98,7 @@ struct Problem {
     std::vector<double> a16, abf;  // A^_ij / s_i rounded to fp16 / bf16
     std::vector<double> rs16, rsbf;// s_i (powers of two; ones without row scaling)
     std::vector<double> m64, m32, m16, mbf;  // M = diag(A^)^{-1} in each precision
+    std::vector<double> ainv_l, ainv_u, ainv_dinv;  // approximate-inverse factors (fp64)
     int diag_scale = 1, row_scale = 0, precond = ORC_PC_JACOBI;
 };
 
@@ -320,11 +321,38 @@ struct Nest {
     /* M v in the caller's arithmetic type (Table 1: M stored in m_prec) */
     template <class T>
     void apply_M(const T *v, T *z) {
+        if (prm.precond == ORC_PC_AINV) {
+            ainv_apply<T>(v, z);
+            m_applies += 1;
+            return;
+        }
         const std::vector<double> &m = m_for(P, prm.m_prec);
         const int n = P.n;
         OMP_FOR
         for (int i = 0; i < n; ++i) z[i] = (T)m[i] * v[i];
         m_applies += 1;
+    }
+
+    /* u = M r with the approximate inverse M = (I - Dt^-1 U) Dt^-1 (I - L Dt^-1),
+     * factors rounded to m_prec, arithmetic in T, row sums in CSR order:
+     * t = Dt^-1 (r - (L Dt^-1) r),  u = t - (Dt^-1 U) t. */
+    template <class T>
+    void ainv_apply(const T *r, T *u) {
+        const int n = P.n;
+        const int mp = prm.m_prec;
+        std::vector<T> t(n);
+        for (int i = 0; i < n; ++i) {
+            T acc = 0;
+            for (int k = P.rp[i]; k < P.rp[i + 1]; ++k)
+                acc = fma_t((T)rnd_prec(mp, P.ainv_l[k]), r[P.ci[k]], acc);
+            t[i] = (T)rnd_prec(mp, P.ainv_dinv[i]) * (r[i] - acc);
+        }
+        for (int i = 0; i < n; ++i) {
+            T acc = 0;
+            for (int k = P.rp[i]; k < P.rp[i + 1]; ++k)
+                acc = fma_t((T)rnd_prec(mp, P.ainv_u[k]), t[P.ci[k]], acc);
+            u[i] = t[i] - acc;
+        }
     }
 
     /* One call of Algorithm 1 (Richardson with adaptive weights).
@@ -360,7 +388,10 @@ struct Nest {
                 spmv_t<TR>(P, prm.rich_a_prec, z.data(), s.data());
                 for (int i = 0; i < n; ++i) r[i] = (TR)rnd_prec(prec, (double)(vr[i] - s[i]));
             }
-            for (int i = 0; i < n; ++i) u[i] = (TR)mv[i] * r[i];
+            if (prm.precond == ORC_PC_AINV)
+                ainv_apply<TR>(r.data(), u.data());
+            else
+                for (int i = 0; i < n; ++i) u[i] = (TR)mv[i] * r[i];
             m_applies += 1;
             if (update) {
                 spmv_t<TR>(P, prm.rich_a_prec, u.data(), w.data());
@@ -583,6 +614,30 @@ void *orc_problem_create(int32_t n, const int32_t *rowptr, const int32_t *colidx
 
 void orc_problem_destroy(void *p) { delete (Problem *)p; }
 
+void orc_problem_set_ainv(void *p, double alpha) {
+    Problem &P = *(Problem *)p;
+    const int n = P.n;
+    std::vector<double> dt(n);
+    for (int i = 0; i < n; ++i) {
+        double dii = 0.0;
+        for (int k = P.rp[i]; k < P.rp[i + 1]; ++k)
+            if (P.ci[k] == i) dii = P.ah[k];
+        dt[i] = (dii != 0.0) ? alpha * dii : alpha;
+    }
+    const size_t nnz = P.ci.size();
+    P.ainv_l.assign(nnz, 0.0);
+    P.ainv_u.assign(nnz, 0.0);
+    P.ainv_dinv.resize(n);
+    for (int i = 0; i < n; ++i) {
+        P.ainv_dinv[i] = 1.0 / dt[i];
+        for (int k = P.rp[i]; k < P.rp[i + 1]; ++k) {
+            const int c = P.ci[k];
+            if (c < i) P.ainv_l[k] = P.ah[k] / dt[c];
+            else if (c > i) P.ainv_u[k] = P.ah[k] / dt[i];
+        }
+    }
+}
+
 int64_t orc_problem_get(void *p, int which, double *out) {
     const Problem &P = *(const Problem *)p;
     const std::vector<double> *src = nullptr;
@@ -598,6 +653,9 @@ int64_t orc_problem_get(void *p, int which, double *out) {
         case 8: src = &P.m32; break;
         case 9: src = &P.m16; break;
         case 10: src = &P.mbf; break;
+        case 11: src = &P.ainv_l; break;
+        case 12: src = &P.ainv_u; break;
+        case 13: src = &P.ainv_dinv; break;
         default: return -1;
     }
     if (out) std::memcpy(out, src->data(), sizeof(double) * src->size());

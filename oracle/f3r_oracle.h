@@ -21,7 +21,7 @@ extern "C" {
 
 /* storage / arithmetic precisions */
 enum { ORC_F64 = 0, ORC_F32 = 1, ORC_F16 = 2, ORC_BF16 = 3 };
-enum { ORC_PC_IDENTITY = 0, ORC_PC_JACOBI = 1 };
+enum { ORC_PC_IDENTITY = 0, ORC_PC_JACOBI = 1, ORC_PC_AINV = 3 };
 enum { ORC_OK = 0, ORC_NOT_CONVERGED = 4, ORC_BREAKDOWN = 5, ORC_NONFINITE = 6, ORC_ERR_ARG = 1 };
 
 typedef struct {
@@ -33,7 +33,7 @@ typedef struct {
     int rich_a_prec;    /* precision of A inside Richardson */
     int rich_v_prec;    /* precision of Richardson vectors (F16, BF16, F32, F64) */
     int m_prec;         /* storage precision of the primary preconditioner M */
-    int precond;        /* ORC_PC_IDENTITY or ORC_PC_JACOBI */
+    int precond;        /* ORC_PC_IDENTITY, ORC_PC_JACOBI or ORC_PC_AINV (needs orc_problem_set_ainv) */
     int c;              /* weight-update period (Algorithm 1) */
     double omega_fixed; /* > 0: fixed Richardson weights, no adaptive update */
     int diag_scale;     /* symmetric diagonal scaling of the inner nest */
@@ -76,6 +76,11 @@ void orc_round(int prec, const double *x, double *y, int64_t n);
 void *orc_problem_create(int32_t n, const int32_t *rowptr, const int32_t *colidx,
                          const double *val, int diag_scale, int row_scale, int precond);
 void orc_problem_destroy(void *p);
+/* approximate inverse M = (I - Dt^-1 U) Dt^-1 (I - L Dt^-1) of the scaled
+ * matrix A^ = L + D + U, Dt = alpha D: factors L Dt^-1 and Dt^-1 U per CSR
+ * entry (zero off their strict triangles) and Dt^-1, exact in fp64; rounded
+ * to m_prec when applied.  orc_problem_get which 11, 12, 13 returns them. */
+void orc_problem_set_ainv(void *p, double alpha);
 /* which: 0 d = D^{-1/2}, 1 scaled A (f64), 2 A f32, 3 A f16 (divided by row scale),
  *        4 A bf16 (divided by row scale), 5 row scale f16, 6 row scale bf16,
  *        7 M f64, 8 M f32, 9 M f16, 10 M bf16 */

@@ -37,7 +37,7 @@ struct OutSlot {
 // Kernel timing slots (kind * 4 + level) for the event profiler.
 enum {
     PK_SPMV_DOTS = 0, PK_CGS_PASS, PK_CGS_FINAL, PK_NORMALIZE, PK_COMBINE, PK_START, PK_M, PK_RICH2,
-    PK_RICH_STEP, PK_RICH_UPD, PK_OUTER_SPMV, PK_OUTER_CGS, PK_OUTER_OTHER, PK_SPMV, PK_CGS_FUSED, PK_KINDS
+    PK_RICH_STEP, PK_RICH_UPD, PK_OUTER_SPMV, PK_OUTER_CGS, PK_OUTER_OTHER, PK_SPMV, PK_CGS_FUSED, PK_STEP, PK_KINDS
 };
 constexpr int kProfSlots = PK_KINDS * 4;
 
@@ -50,6 +50,11 @@ struct ProfRec {
 // (G == 0: not fused).
 struct FusedPlan {
     int G = 0, chunk = 0, smem = 0;
+};
+
+// Launch shape of the whole-iteration kernel of the innermost level (G == 0: off).
+struct StepPlan {
+    int G = 0, S = 0, stage_bytes = 0, smem = 0;
 };
 
 struct Ctx {
@@ -72,6 +77,10 @@ struct Ctx {
     float *rs = nullptr;        // power-of-two row scales s (row_scale = 1)
     double *dsc = nullptr;      // D^-1/2
     void *mvec = nullptr;       // M in m_prec
+    // approximate inverse M = (I - Dt^-1 U) Dt^-1 (I - L Dt^-1) (precond = F3R_PC_AINV)
+    h16 *ainv_l = nullptr, *ainv_u = nullptr;  // L Dt^-1 and Dt^-1 U on the SELL pattern (fp16)
+    h16 *ainv_dinv = nullptr;                  // Dt^-1 (fp16)
+    float *ainv_t = nullptr, *ainv_m = nullptr;  // Dt^-1 (I - L Dt^-1) r and M r (fp32)
     LevelHost L[4];
     // Richardson
     void *rin = nullptr, *rz[2] = {nullptr, nullptr}, *rr = nullptr;
@@ -86,6 +95,8 @@ struct Ctx {
     unsigned *ticket = nullptr;
     unsigned *coop = nullptr;   // grid-barrier counters of cooperative launches (zero between launches)
     FusedPlan fplan[4];
+    StepPlan stplan;
+    int stplan_bps = 0;         // blocks per SM the step plan is being tried with
     int G = 1, Gs = 1, G1 = 1, Gv = 1;  // grids: elementwise, SpMV, outer CGS, streaming vector kernels
     int *flags = nullptr;       // 4 ints per level
     int *err = nullptr;         // device error word (bounded waits that gave up)
@@ -157,6 +168,7 @@ void launch_cgs_final(Ctx &c, int d, int j, bool last, cudaStream_t s);
 void plan_cgs_fused(Ctx &c);
 bool launch_cgs_fused(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_t s);
 bool launch_outer_cgs_fused(Ctx &c, cudaStream_t s);
+bool launch_f3_step(Ctx &c, int d, int j, bool last, bool update, cudaStream_t s);
 void launch_combine(Ctx &c, int d, const OutSlot &o, cudaStream_t s);
 void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s);
 void launch_outer_residual(Ctx &c, const double *b, const double *x, bool compute_nb, cudaStream_t s);
@@ -176,6 +188,9 @@ f3r_status learned_loss_grad(Ctx &c, const float *R, const float *E, int P, cuda
 void learned_adam(Ctx &c, float lr, cudaStream_t s);
 void learned_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s);
 void learned_free(Ctx &c);
+
+// ainv.cu: Richardson call with the approximate inverse as M
+void ainv_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s);
 f3r_status learned_set_loss(Ctx &c, int kind);
 int learned_loss_kind(const Ctx &c);
 float *learned_theta(Ctx &c);

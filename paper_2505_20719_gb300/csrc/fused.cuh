@@ -80,9 +80,9 @@ template <class T> struct FusedScratch {
 
 // block-wide sums of acc[0..nd) (and a max in acc[nd] when with_max) in warp
 // order; thread d < nd (+1) returns its total through out
-template <class T, int ND>
+template <class T, int ND, int NW = kFusedWarps>
 __device__ __forceinline__ void block_reduce(T (&acc)[ND], int nd, bool with_max, T *out) {
-    __shared__ T sm[ND][kFusedWarps];
+    __shared__ T sm[ND][NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ntot = nd + (with_max ? 1 : 0);
 #pragma unroll
@@ -95,7 +95,7 @@ __device__ __forceinline__ void block_reduce(T (&acc)[ND], int nd, bool with_max
     if (threadIdx.x < ntot) {
         const int d = threadIdx.x;
         T s = sm[d][0];
-        for (int w = 1; w < kFusedWarps; ++w) s = (with_max && d == nd) ? fmax(s, sm[d][w]) : add_rn(s, sm[d][w]);
+        for (int w = 1; w < NW; ++w) s = (with_max && d == nd) ? fmax(s, sm[d][w]) : add_rn(s, sm[d][w]);
         out[d] = s;
     }
     __syncthreads();

@@ -4,6 +4,7 @@
 // the three separate kernels).
 #include "ctx.h"
 #include "fused.cuh"
+#include "step.cuh"
 
 namespace f3r {
 
@@ -175,13 +176,107 @@ bool outer_dispatch(Ctx &c, cudaStream_t s, bool plan_only) {
     return false;
 }
 
+// ---------------------------------------------------------------- whole step
+bool step_eligible(const Ctx &c, int d) {
+    const f3r_params &p = c.prm;
+    return p.fuse_cgs && c.coop && d >= 1 && d == p.nlevels - 1 && c.L[d].child == CHILD_R &&
+           c.L[d].v_prec == F3R_F32 && c.L[d].a_prec == F3R_F16 && p.rich_m == 2 && p.rich_v_prec == F3R_F16 &&
+           p.rich_a_prec == F3R_F16 && p.m_prec == F3R_F16 && p.precond == F3R_PC_JACOBI && c.a16;
+}
+
+template <int S, int MAXD> bool step_go(Ctx &c, int d, int j, bool last, cudaStream_t s, bool plan_only) {
+    auto kern = k_f3_step<S, MAXD>;
+    if (plan_only) {
+        // the first (blocks per SM, ring depth S) that fits, more blocks first
+        StepPlan p = c.stplan;
+        if (p.G > 0) return true;
+        const StagePlan sp = plan_stage(c, sizeof(h16), c.L[d].m, sizeof(float));
+        if (sp.S == 0) return false;
+        const int ntiles = ceil_div(c.nslices, kTileSlices);
+        for (int bps = c.stplan_bps; bps >= c.stplan_bps; --bps) {
+            const int G = std::min(c.nsm * bps, ntiles);
+            const int per = ceil_div(ntiles, G);
+            const long long smem = kBarBytes + (long long)S * sp.stage_bytes + (long long)per * kTileRows * 4;
+            if (smem > 220 * 1024) continue;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStagedThreads, (int)smem) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (nb < bps) continue;
+            p.G = G;
+            p.S = S;
+            p.stage_bytes = sp.stage_bytes;
+            p.smem = (int)smem;
+            break;
+        }
+        c.stplan = p;
+        return p.G > 0;
+    }
+    const StepPlan p = c.stplan;
+    if (p.G == 0 || p.S != S) return false;
+    StepArgs a;
+    a.A = sell_of(c);
+    a.a16 = c.a16;
+    a.rs = c.prm.row_scale ? c.rs : nullptr;
+    a.v16 = (const h16 *)c.rin;
+    a.m16 = (const h16 *)c.mvec;
+    a.zout = (float *)c.L[d].Z + (size_t)j * c.ld;
+    a.omega = (const float *)c.omega;
+    a.counters = c.counters;
+    a.v16_next = (h16 *)c.rin;
+    a.stage_bytes = p.stage_bytes;
+    a.err = c.err;
+    a.bar = c.coop;
+    a.part = (float *)c.partials;
+    const int do_norm = (j < c.L[d].m - 1) ? 1 : 0;
+    return launch_coop(kern, dim3(p.G), dim3(kStagedThreads), p.smem, s, a, levdev_inner<float>(c, d), j, last ? 1 : 0,
+                       want_sigma_of(c, d), do_norm) == cudaSuccess;
+}
+
+bool step_dispatch(Ctx &c, int d, int j, bool last, cudaStream_t s, bool plan_only, int S_try = 0) {
+    const int md = maxd_bucket(c.L[d].m);
+    const int S = plan_only ? S_try : c.stplan.S;
+    if (S == 3) {
+        if (md == 4) return step_go<3, 4>(c, d, j, last, s, plan_only);
+        if (md == 8) return step_go<3, 8>(c, d, j, last, s, plan_only);
+        return step_go<3, 16>(c, d, j, last, s, plan_only);
+    }
+    if (S == 2) {
+        if (md == 4) return step_go<2, 4>(c, d, j, last, s, plan_only);
+        if (md == 8) return step_go<2, 8>(c, d, j, last, s, plan_only);
+        return step_go<2, 16>(c, d, j, last, s, plan_only);
+    }
+    return false;
+}
+
 }  // namespace
+
+bool launch_f3_step(Ctx &c, int d, int j, bool last, bool update, cudaStream_t s) {
+    if (update || c.stplan.G == 0 || d != c.prm.nlevels - 1) return false;
+    prof_begin(c, PK_STEP, d, s);
+    step_dispatch(c, d, j, last, s, false);
+    prof_end(c, s);
+    c.launches++;
+    return true;
+}
 
 void plan_cgs_fused(Ctx &c) {
     for (int d = 0; d < 4; ++d) c.fplan[d] = FusedPlan{};
     if (!c.prm.fuse_cgs || !c.coop) return;
     outer_dispatch(c, nullptr, true);
     for (int d = 1; d < c.prm.nlevels; ++d) fused_dispatch(c, d, 0, false, false, nullptr, true);
+    c.stplan = StepPlan{};
+    const int d = c.prm.nlevels - 1;
+    if (!c.prm.fuse_step || !step_eligible(c, d)) return;
+    for (int bps = 4; bps >= 1 && c.stplan.G == 0; --bps) {
+        c.stplan_bps = bps;
+        for (int S = 3; S >= 2 && c.stplan.G == 0; --S) step_dispatch(c, d, 0, false, nullptr, true, S);
+    }
 }
 
 bool launch_outer_cgs_fused(Ctx &c, cudaStream_t s) {

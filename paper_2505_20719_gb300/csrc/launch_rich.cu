@@ -84,6 +84,12 @@ static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const 
 
 void launch_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_misc, cudaStream_t s) {
     const int a = c.prm.rich_a_prec, v = c.prm.rich_v_prec;
+    if (c.prm.precond == F3R_PC_AINV) {
+        prof_begin(c, PK_RICH_STEP, 2, s);
+        ainv_rich_call(c, update, pos, out, par_misc, s);
+        prof_end(c, s);
+        return;
+    }
     if (c.prm.precond == F3R_PC_LEARNED && c.learned) {
         prof_begin(c, PK_RICH_STEP, 1, s);
         learned_rich_call(c, update, pos, out, par_misc, s);

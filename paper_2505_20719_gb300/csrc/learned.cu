@@ -11,6 +11,7 @@
 #include "ctx.h"
 #include "learned.cuh"
 #include "rich.cuh"
+#include "rich_u.cuh"
 
 namespace f3r {
 namespace lm {
@@ -508,63 +509,6 @@ __global__ void __launch_bounds__(kBlock) k_lm_h2f(const h16 *x, float *y, int n
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = __half2float(x[i]);
 }
 
-// Richardson update with the learned M: z = fp16(fma(w, u, z_prev)), u = M_theta(r);
-// the last step writes the parent's output z / sigma.  With want_w, w is the
-// locally optimal weight computed by k_lm_upd_w.
-__global__ void __launch_bounds__(kBlock) k_lm_rich_z(const float *u, const h16 *zprev, h16 *znext, float *out,
-                                                      const float *par_misc, const float *omega, const float *wcur,
-                                                      int k, int last, int use_wcur, const int *flags,
-                                                      int check_depth, int n, unsigned long long *counters) {
-    pdl_enter();
-    if (stopped(flags, check_depth)) return;
-    const float w = use_wcur ? *wcur : omega[k];
-    const float inv_sigma = par_misc[MS_INV_SIGMA];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float zp = zprev ? __half2float(zprev[i]) : 0.0f;
-        const float z = rnd<h16>(fma_rn(w, u[i], zp));
-        if (last) out[i] = mul_rn(z, inv_sigma);
-        else znext[i] = __float2half_rn(z);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        atomicAdd(counters + 0, 1ull);
-        if (last) {
-            atomicAdd(counters + 1, 1ull);
-            if (use_wcur) atomicAdd(counters + 2, 1ull);
-        }
-    }
-}
-
-// update step with the learned M: w = A^ u, w' = (r, w)/(w, w), weight average
-__global__ void __launch_bounds__(kBlock) k_lm_upd_w(Sell S, const h16 *__restrict__ a16, const float *__restrict__ rs,
-                                                     const h16 *__restrict__ r, const float *__restrict__ u, float *omega,
-                                                     float *wcur, const long long *c_ntr_base, int k, int pos, int c,
-                                                     GridRed<float> gr, const int *flags, int check_depth, int n) {
-    pdl_enter();
-    if (stopped(flags, check_depth)) return;
-    float acc[2] = {0.0f, 0.0f};
-    const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int s = wid; s < S.nslices; s += nw) {
-        float w = sell_row<float>(S, a16, s, lane, [&](int cc) { return u[cc]; });
-        const int i = s * kSlice + lane;
-        if (rs) w = mul_rn(w, rs[i]);
-        if (i < n) {
-            acc[0] = fma_rn(__half2float(r[i]), w, acc[0]);
-            acc[1] = fma_rn(w, w, acc[1]);
-        }
-    }
-    grid_reduce<float, 2>(acc, 2, false, gr, [&](float *res) {
-        const float wk = omega[k];
-        const float q = div_rn(res[0], res[1]);
-        const bool ok = res[1] > 0.0f && isfinite(q);
-        *wcur = ok ? q : wk;
-        if (ok) {
-            const float l = (float)((*c_ntr_base + pos) / c);
-            omega[k] = div_rn(add_rn(mul_rn(l, wk), q), add_rn(l, 1.0f));
-        }
-    });
-}
 
 }  // namespace lm
 
@@ -766,12 +710,12 @@ void learned_rich_call(Ctx &c, bool update, int pos, void *out, const void *par_
         launch_pdl(lm::k_lm_h2f, dim3(c.G), dim3(kBlock), 0, s, rk, L.r32, n, (const int *)c.flags, cd);
         learned_forward(c, L.r32, L.zbuf, false, s);
         if (update) {
-            launch_pdl(lm::k_lm_upd_w, dim3(c.Gs), dim3(kBlock), 0, s, S, (const h16 *)c.a16, rs, rk,
+            launch_pdl(k_rich_upd_w_u, dim3(c.Gs), dim3(kBlock), 0, s, S, (const h16 *)c.a16, rs, rk,
                        (const float *)L.zbuf, (float *)c.omega, (float *)c.wcur, (const long long *)c.c_ntr_base, k, pos,
                        c.prm.c, GridRed<float>{(float *)c.partials, c.ticket, kMaxDots}, (const int *)c.flags, cd, n);
             c.launches++;
         }
-        launch_pdl(lm::k_lm_rich_z, dim3(c.G), dim3(kBlock), 0, s, (const float *)L.zbuf, zp, zb[k & 1], (float *)out,
+        launch_pdl(k_rich_z_u, dim3(c.G), dim3(kBlock), 0, s, (const float *)L.zbuf, zp, zb[k & 1], (float *)out,
                    (const float *)par_misc, (const float *)c.omega, (const float *)c.wcur, k, last ? 1 : 0,
                    update ? 1 : 0, (const int *)c.flags, cd, n, c.counters);
         c.launches += 2;

@@ -117,6 +117,46 @@ __global__ void k_fill(const int *rp, const int *ci, const double *val, int n, i
     }
 }
 
+// Factors of the approximate inverse M = (I - Dt^-1 U) Dt^-1 (I - L Dt^-1) of
+// A^ = L + D + U, Dt = alpha D: entry (i, c) of L Dt^-1 is A^_ic / dt_c
+// (c < i), of Dt^-1 U it is A^_ic / dt_i (c > i), both rounded to fp16 once
+// from fp64 (zero elsewhere on the SELL pattern); Dt^-1 in fp16.  A^_ic is
+// formed as (a_ic d_i) d_c, the set-up's own rounding of the scaled matrix.
+__global__ void k_ainv_fill(const int *rp, const int *ci, const double *val, int n, const int *sptr,
+                            const double *dsc, double alpha, h16 *wl, h16 *wu, h16 *dinv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = i / kSlice, lane = i % kSlice;
+        const int base = sptr[s] + lane;
+        const int w = (sptr[s + 1] - sptr[s]) / kSlice;
+        const int b = rp[i], len = rp[i + 1] - b;
+        const double di = dsc[i];
+        double dii = 0.0;
+        for (int k = 0; k < len; ++k)
+            if (ci[b + k] == i) dii = (val[b + k] * di) * di;
+        const double dti = (dii != 0.0) ? alpha * dii : alpha;
+        dinv[i] = __double2half(div_rn(1.0, dti));
+        for (int k = 0; k < w; ++k) {
+            const int idx = base + k * kSlice;
+            double l = 0.0, u = 0.0;
+            if (k < len) {
+                const int c = ci[b + k];
+                const double ah = (val[b + k] * di) * dsc[c];
+                if (c < i) {
+                    double dcc = 0.0;
+                    for (int q = rp[c]; q < rp[c + 1]; ++q)
+                        if (ci[q] == c) dcc = (val[q] * dsc[c]) * dsc[c];
+                    const double dtc = (dcc != 0.0) ? alpha * dcc : alpha;
+                    l = div_rn(ah, dtc);
+                } else if (c > i) {
+                    u = div_rn(ah, dti);
+                }
+            }
+            wl[idx] = __double2half(l);
+            wu[idx] = __double2half(u);
+        }
+    }
+}
+
 template <class S>
 __global__ void k_export(const int *rp, int n, const int *sptr, const S *src, S *dst) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -193,6 +233,18 @@ f3r_status build_matrix(Ctx &c, const int *rp, const int *ci, const double *val,
     const int gf = std::max(1, std::min(ceil_div((long long)c.nslices * kSlice, kBlock), c.nsm * 8));
     k_fill<<<gf, kBlock, 0, s>>>(rp, ci, val, n, c.nslices, c.sptr, c.dsc, c.prm.row_scale, c.prm.precond,
                                  c.prm.m_prec, c.col, c.a64, c.ah64, c.a32, c.a16, c.abf, c.rs, c.mvec);
+    if (c.prm.precond == F3R_PC_AINV) {
+        c.ainv_l = (h16 *)dalloc(c, sizeof(h16) * tot);
+        c.ainv_u = (h16 *)dalloc(c, sizeof(h16) * tot);
+        c.ainv_dinv = (h16 *)dalloc(c, sizeof(h16) * (size_t)c.nslices * kSlice);
+        c.ainv_t = (float *)dalloc(c, sizeof(float) * (size_t)c.nslices * kSlice);
+        c.ainv_m = (float *)dalloc(c, sizeof(float) * (size_t)c.nslices * kSlice);
+        if (!c.ainv_l || !c.ainv_u || !c.ainv_dinv || !c.ainv_t || !c.ainv_m) return F3R_ERR_NOMEM;
+        cudaMemsetAsync(c.ainv_l, 0, sizeof(h16) * tot, s);
+        cudaMemsetAsync(c.ainv_u, 0, sizeof(h16) * tot, s);
+        k_ainv_fill<<<grid, kBlock, 0, s>>>(rp, ci, val, n, c.sptr, c.dsc, (double)c.prm.ainv_alpha, c.ainv_l,
+                                            c.ainv_u, c.ainv_dinv);
+    }
     c.rowptr = (int *)dalloc(c, sizeof(int) * (n + 1));
     if (!c.rowptr) return F3R_ERR_NOMEM;
     cudaMemcpyAsync(c.rowptr, rp, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s);
@@ -241,6 +293,18 @@ f3r_status export_array(Ctx &c, int which, void *out, cudaStream_t s) {
             return cudaStreamSynchronize(s) == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
         case 6:
             cudaMemcpyAsync(out, c.mvec, (size_t)prec_bytes(c.prm.m_prec) * n, cudaMemcpyDeviceToHost, s);
+            return cudaStreamSynchronize(s) == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
+        case 7:
+            if (!c.ainv_l) return F3R_ERR_ARG;
+            run(c.ainv_l, sizeof(h16));
+            break;
+        case 8:
+            if (!c.ainv_u) return F3R_ERR_ARG;
+            run(c.ainv_u, sizeof(h16));
+            break;
+        case 9:
+            if (!c.ainv_dinv) return F3R_ERR_ARG;
+            cudaMemcpyAsync(out, c.ainv_dinv, sizeof(h16) * n, cudaMemcpyDeviceToHost, s);
             return cudaStreamSynchronize(s) == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
         default:
             return F3R_ERR_ARG;

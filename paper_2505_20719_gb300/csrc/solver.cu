@@ -76,7 +76,13 @@ f3r_status check_params(const f3r_params &p) {
     if (p.c < 1 || p.max_outer < 1 || !(p.tol >= 0.0)) return F3R_ERR_ARG;
     if (p.cgs_passes != 1 && p.cgs_passes != 2) return F3R_ERR_ARG;
     if (!(p.inner_rtol >= 0.0f && p.inner_rtol < 1.0f)) return F3R_ERR_ARG;
-    if (p.precond != F3R_PC_IDENTITY && p.precond != F3R_PC_JACOBI && p.precond != F3R_PC_LEARNED) return F3R_ERR_ARG;
+    if (p.precond != F3R_PC_IDENTITY && p.precond != F3R_PC_JACOBI && p.precond != F3R_PC_LEARNED &&
+        p.precond != F3R_PC_AINV)
+        return F3R_ERR_ARG;
+    if (p.precond == F3R_PC_AINV &&
+        (p.rich_m < 1 || p.rich_v_prec != F3R_F16 || p.rich_a_prec != F3R_F16 || p.m_prec != F3R_F16 ||
+         p.row_scale || !(p.ainv_alpha > 0.0f)))
+        return F3R_ERR_UNSUPPORTED;
     if (p.precond == F3R_PC_LEARNED &&
         (p.rich_m < 1 || p.rich_v_prec != F3R_F16 || p.rich_a_prec != F3R_F16 || p.row_scale))
         return F3R_ERR_UNSUPPORTED;
@@ -153,6 +159,11 @@ void run_level(Ctx &c, int d, const OutSlot &out, long long &pos, cudaStream_t s
             o.prec = L.v_prec;
             run_level(c, d + 1, o, pos, s);
         } else if (L.child == CHILD_R) {
+            // the whole iteration in one cooperative launch when it applies
+            if (launch_f3_step(c, d, j, j == L.m - 1, is_update(c, pos), s)) {
+                ++pos;
+                continue;
+            }
             launch_rich_call(c, is_update(c, pos), (int)pos, zslot(c, d, j), misc_of(c, d), s);
             ++pos;
         } else {
@@ -278,6 +289,8 @@ f3r_status f3r_default_params(f3r_params *p) {
     p->use_graphs = 1;
     p->keep_omega = 0;
     p->fuse_cgs = 1;
+    p->fuse_step = 0;
+    p->ainv_alpha = 1.0f;
     return F3R_OK;
 }
 
@@ -706,7 +719,7 @@ int f3r_profile_slots(void) { return kProfSlots; }
 const char *f3r_profile_slot_name(int slot) {
     static const char *names[PK_KINDS] = {"spmv_dots", "cgs_pass", "cgs_final", "normalize", "combine",
                                           "level_start", "apply_M", "rich_fused2", "rich_step", "rich_update",
-                                          "outer_spmv", "outer_cgs", "outer_other", "spmv", "cgs_fused"};
+                                          "outer_spmv", "outer_cgs", "outer_other", "spmv", "cgs_fused", "f3_step"};
     if (slot < 0 || slot >= kProfSlots) return "";
     return names[slot / 4];
 }

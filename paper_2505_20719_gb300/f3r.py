@@ -15,12 +15,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libf3r.so")
 
 F64, F32, F16, BF16 = 0, 1, 2, 3
-PC_IDENTITY, PC_JACOBI, PC_LEARNED = 0, 1, 2
+PC_IDENTITY, PC_JACOBI, PC_LEARNED, PC_AINV = 0, 1, 2, 3
 KRYLOV_CG, KRYLOV_BICGSTAB = 1, 2
 LEARNED_NPARAMS = 6337
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of memory", 4: "not converged",
           5: "breakdown", 6: "non-finite value", 7: "device wait timed out", 8: "unsupported"}
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, NOT_CONVERGED, ERR_BREAKDOWN, ERR_NONFINITE = 0, 1, 2, 3, 4, 5, 6
+ERR_TIMEOUT, ERR_UNSUPPORTED = 7, 8
 
 
 class F3RError(RuntimeError):
@@ -36,7 +37,8 @@ class Params(C.Structure):
         ("precond", C.c_int), ("c", C.c_int), ("omega_fixed", C.c_double), ("diag_scale", C.c_int),
         ("row_scale", C.c_int), ("scale_cast", C.c_int), ("cgs_passes", C.c_int), ("tol", C.c_double),
         ("max_outer", C.c_int), ("use_graphs", C.c_int), ("keep_omega", C.c_int), ("fuse_cgs", C.c_int),
-        ("inner_rtol", C.c_float), ("reserved", C.c_int * 5),
+        ("inner_rtol", C.c_float), ("ainv_alpha", C.c_float),
+        ("fuse_step", C.c_int), ("reserved", C.c_int * 3),
     ]
 
 
@@ -290,7 +292,8 @@ class Solver:
 
     def export(self, which: int, nnz: int = None) -> np.ndarray:
         """Set-up arrays in CSR order: 0 d, 1 A^ f64, 2 A^ f32, 3 A^/s f16 bits,
-        4 A^/s bf16 bits, 5 row scales, 6 M (m_prec)."""
+        4 A^/s bf16 bits, 5 row scales, 6 M (m_prec); approximate inverse:
+        7 L Dt^-1, 8 Dt^-1 U (f16 bits, nnz), 9 Dt^-1 (f16 bits, n)."""
         n = self.n
         if which == 0:
             out = np.empty(n, np.float64)
@@ -298,8 +301,10 @@ class Solver:
             out = np.empty(nnz, np.float64)
         elif which == 2:
             out = np.empty(nnz, np.float32)
-        elif which in (3, 4):
+        elif which in (3, 4, 7, 8):
             out = np.empty(nnz, np.uint16)
+        elif which == 9:
+            out = np.empty(n, np.uint16)
         elif which == 5:
             out = np.empty(n, np.float32)
         else:

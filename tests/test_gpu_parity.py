@@ -374,13 +374,15 @@ def test_invalid_matrix_rejected():
 
 
 @pytest.mark.parametrize("kind", ["fp16", "fp64"])
-def test_fused_and_unfused_cgs_agree(kind):
-    """The fused CGS2 / normalisation launch changes only the summation order
-    of the dot products: both paths converge alike and match the oracle."""
+@pytest.mark.parametrize("step", [1, 0])
+def test_fused_and_unfused_cgs_agree(kind, step):
+    """The fused CGS2 / normalisation launch (and, for fp16, the whole-iteration
+    launch of the innermost level) changes only the summation order of the
+    dot products: both paths converge alike and match the oracle."""
     prob = G.diffusion3d_7pt(dims=(40, 36, 30), seed=108)
     out = {}
     for fuse in (0, 1):
-        s = solver(prob, _rich_prm(kind, fuse_cgs=fuse))
+        s = solver(prob, _rich_prm(kind, fuse_cgs=fuse, fuse_step=step))
         x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
         out[fuse] = (s.solve(dev(prob.b), x), x.cpu().numpy())
     P = O.Problem(prob, diag_scale=1)
