@@ -9,7 +9,7 @@ stream.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
---impl reference times the CPU oracle (the reference arm of this build) on a
+--impl reference times the CPU oracle (the plain reference implementation) on a
 bounded sample of the same workload.  With N > 1 (torchrun) every rank solves
 its own replica of the workload (no collective on the data path).
 """
@@ -103,22 +103,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _src_hash():
+def _src_hash(files=None):
+    """Hash of the kernel sources (all of csrc/, or the listed files there)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2505_20719_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files or os.listdir(d)):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel sources."""
+    was taken on the current sources of that kernel (the files it is built
+    from, listed with the capture)."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
         e = t.get(kernel)
-        if e and e.get("src_sha") == _src_hash():
+        if e and e.get("src_sha") == _src_hash(e.get("files")):
             return e.get("bytes_per_launch")
     except Exception:
         pass

@@ -1,7 +1,7 @@
 // Approximate inverse as the primary preconditioner M of the Richardson level
 // (the paper's GPU runs use SD-AINV, a simplified approximate inverse that
 // costs two SpMVs per application, Sec. 5.2; its construction is in a cited
-// work).  This build's approximate inverse truncates the inverse of the
+// work).  The approximate inverse here truncates the inverse of the
 // triangular factors of A^ ~ (Dt + L) Dt^-1 (Dt + U) after the first term:
 //     M = (I - Dt^-1 U) Dt^-1 (I - L Dt^-1),   Dt = alpha diag(A^),
 // with L Dt^-1, Dt^-1 U and Dt^-1 stored in fp16 on the SELL pattern of A^.

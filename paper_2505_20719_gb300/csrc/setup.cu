@@ -1,4 +1,4 @@
-// Setup (SURVEY step a1): validate the CSR matrix, symmetric diagonal scaling
+// Setup: validate the CSR matrix, symmetric diagonal scaling
 // (Sec. 5), conversion to sliced ELLPACK with 32-row slices (Sec. 5.2) and the
 // fp64 / fp32 / fp16 / bf16 copies of the scaled matrix (Table 1).  Runs on
 // the device after one upload of the CSR arrays.
