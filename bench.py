@@ -134,6 +134,17 @@ def _dist():
     return ws, rank, local
 
 
+def replica_max(value, device):
+    """The maximum of `value` over all ranks (each rank times its own replica;
+    the job's time is the slowest rank's), then a barrier."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def cpu_baseline(prob, kind, outer_iters, max_seconds=25.0):
     """The oracle as it stands, timed on this host's cores on a bounded sample:
     whole outer iterations of the same solve (x0 = 0), scaled to the number of
@@ -525,10 +536,7 @@ def main():
     clocks = sampler.stop()
     total_ms = sum(times)
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        total_ms = float(t.item())
+        total_ms = replica_max(total_ms, dev)
     last = results[-1]
     A = prob.to_scipy()
     xh = x.cpu().numpy()
