@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8) ? 2 : 1)
 constexpr int kOuterGroup = 8;
 
 template <class TC, int CHILD>
-__global__ void __launch_bounds__(kFusedThreads, 1)
+__global__ void __launch_bounds__(kFusedThreads, 2)
     k_outer_cgs_fused(LevelDev<double> L, int passes, ChildOut<TC> co, FusedScratch<double> fs, GridRed<TC> grc) {
     constexpr int N = 2;  // double2 packs
     extern __shared__ __align__(16) unsigned char fused_dsm[];

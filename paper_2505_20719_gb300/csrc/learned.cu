@@ -81,19 +81,35 @@ __device__ __forceinline__ void aggregate16(const Sell &A, const h16 *__restrict
     const int s = i >> 5, li = i & 31;
     const int beg = __ldg(A.sptr + s) + li;
     const int w = (__ldg(A.sptr + s + 1) - __ldg(A.sptr + s)) >> 5;
-    for (int k = 0; k < w; ++k) {
-        const int idx = beg + (k << 5);
-        const int c = __ldg(A.col + idx);
-        if (c >= 0 && c != i) {
-            const float a = __half2float(a16[idx]);
-            const Pack<b16, 8> x0 = ldp<b16, 8>(X + (size_t)c * W + hf * 16);
-            const Pack<b16, 8> x1 = ldp<b16, 8>(X + (size_t)c * W + hf * 16 + 8);
+    // neighbours in groups of kAggGroup: their rows are loaded before the
+    // multiply-adds (each feature still sums in CSR order)
+    constexpr int kAggGroup = 4;
+    for (int k0 = 0; k0 < w; k0 += kAggGroup) {
+        int c[kAggGroup];
+        float a[kAggGroup];
+        Pack<b16, 8> x0[kAggGroup], x1[kAggGroup];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                acc[e] = fma_rn(a, __bfloat162float(x0.v[e]), acc[e]);
-                acc[8 + e] = fma_rn(a, __bfloat162float(x1.v[e]), acc[8 + e]);
-            }
+        for (int q = 0; q < kAggGroup; ++q) {
+            const int idx = beg + ((k0 + q) << 5);
+            const int cc = (k0 + q < w) ? __ldg(A.col + idx) : -1;
+            c[q] = (cc >= 0 && cc != i) ? cc : -1;
+            a[q] = (c[q] >= 0) ? __half2float(a16[idx]) : 0.0f;
         }
+#pragma unroll
+        for (int q = 0; q < kAggGroup; ++q)
+            if (c[q] >= 0) {
+                x0[q] = ldp<b16, 8>(X + (size_t)c[q] * W + hf * 16);
+                x1[q] = ldp<b16, 8>(X + (size_t)c[q] * W + hf * 16 + 8);
+            }
+#pragma unroll
+        for (int q = 0; q < kAggGroup; ++q)
+            if (c[q] >= 0) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    acc[e] = fma_rn(a[q], __bfloat162float(x0[q].v[e]), acc[e]);
+                    acc[8 + e] = fma_rn(a[q], __bfloat162float(x1[q].v[e]), acc[8 + e]);
+                }
+            }
     }
     if (rs) {
         const float sc = rs[i];
