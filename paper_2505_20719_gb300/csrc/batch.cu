@@ -79,9 +79,10 @@ struct LS {
 };
 
 struct Shared {
-    double red_blk[kRedMax];   // this block's partial sums
-    double red_res[kRedMax];   // rank 0: the team's sums
+    double red_blk[2][kRedMax];  // this block's partial sums (two buffers, alternating)
+    double red_res[kRedMax];     // the team's sums, formed by every block itself
     double wred[kRedMax][kBW];
+    int red_buf;                 // buffer of the next reduction
     LS ls2, ls3;
     float omega[2];
     long long c_ntr;
@@ -106,11 +107,17 @@ __device__ __forceinline__ h16 ldcg(const h16 *p) {
 }
 
 // Deterministic team reduction of nd sums (nd <= kRedMax), or maxima where
-// is_max; every thread of the team returns the results in out[].
+// is_max; every thread of the team returns the results in out[].  Each block
+// writes its partials, one cluster barrier, then every block sums all ranks'
+// partials in rank order itself (the same order everywhere, so the same
+// result).  The partials alternate between two buffers: a block still
+// reading the previous reduction's buffer cannot be overtaken, because the
+// next write to that buffer follows one more cluster barrier.
 template <class T>
 __device__ void team_reduce(const Team &tm, Shared &sh, T *acc, int nd, T *out, const bool *is_max = nullptr) {
     cg::cluster_group cl = cg::this_cluster();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int buf = sh.red_buf;
     for (int d = 0; d < nd; ++d) {
         const bool mx = is_max && is_max[d];
         T v = mx ? warp_max(acc[d]) : warp_sum(acc[d]);
@@ -122,23 +129,24 @@ __device__ void team_reduce(const Team &tm, Shared &sh, T *acc, int nd, T *out, 
         const bool mx = is_max && is_max[d];
         T s = (T)sh.wred[d][0];
         for (int w = 1; w < kBW; ++w) s = mx ? fmax(s, (T)sh.wred[d][w]) : add_rn(s, (T)sh.wred[d][w]);
-        sh.red_blk[d] = (double)s;
+        sh.red_blk[buf][d] = (double)s;
     }
     team_sync();
-    if (tm.rank == 0 && threadIdx.x < nd) {
+    if (threadIdx.x < nd) {
         const int d = threadIdx.x;
         const bool mx = is_max && is_max[d];
         T s = (T)0;
         for (unsigned r = 0; r < tm.size; ++r) {
-            const double *rb = cl.map_shared_rank(sh.red_blk, r);
+            const double *rb = cl.map_shared_rank(&sh.red_blk[buf][0], r);
             s = (r == 0) ? (T)rb[d] : (mx ? fmax(s, (T)rb[d]) : add_rn(s, (T)rb[d]));
         }
         sh.red_res[d] = (double)s;
     }
-    team_sync();
-    const double *res0 = cl.map_shared_rank(sh.red_res, 0);
-    for (int d = 0; d < nd; ++d) out[d] = (T)res0[d];
-    team_sync();
+    __syncthreads();
+    for (int d = 0; d < nd; ++d) out[d] = (T)sh.red_res[d];
+    __syncthreads();
+    if (threadIdx.x == 0) sh.red_buf = buf ^ 1;
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- Givens
@@ -662,6 +670,8 @@ __global__ void __launch_bounds__(kBT) k_batch(const Sys *sys, const Inst *inst,
     tm.wid = tm.tid >> 5;
     tm.nwarps = tm.nthr >> 5;
     tm.lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) sh.red_buf = 0;  // every block of the team toggles it in step
+    __syncthreads();
     for (;;) {
         if (tm.rank == 0 && threadIdx.x == 0) sh.inst = atomicAdd(queue, 1);
         team_sync();
