@@ -77,6 +77,7 @@ struct Ctx {
     float *rs = nullptr;        // power-of-two row scales s (row_scale = 1)
     double *dsc = nullptr;      // D^-1/2
     void *mvec = nullptr;       // M in m_prec
+    bool m_unit = false;        // every stored entry of M is exactly 1 (M = I)
     // approximate inverse M = (I - Dt^-1 U) Dt^-1 (I - L Dt^-1) (precond = F3R_PC_AINV)
     h16 *ainv_l = nullptr, *ainv_u = nullptr;  // L Dt^-1 and Dt^-1 U on the SELL pattern (fp16)
     h16 *ainv_dinv = nullptr;                  // Dt^-1 (fp16)

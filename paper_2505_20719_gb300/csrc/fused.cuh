@@ -32,15 +32,20 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     return v;
 }
 
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier of a cooperative launch: arrival number `target` on the
-// monotone counter `arrive` (G per barrier).  Returns false (in every thread
-// of the block) when the wait gave up.
+// monotone counter `arrive` (G per barrier).  Thread 0 arrives with a release
+// reduction (cumulative over the block's writes ordered before it by the
+// block barrier) and polls with acquire loads.  Returns false (in every
+// thread of the block) when the wait gave up.
 __device__ __forceinline__ bool coop_sync(unsigned *arrive, unsigned target, int *err) {
     __shared__ int ok_sh;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(arrive, 1u);
+        red_release_add_u32(arrive, 1u);
         int ok = 1;
         const long long t0 = clock64();
         while (ld_acquire_u32(arrive) < target) {
@@ -51,7 +56,6 @@ __device__ __forceinline__ bool coop_sync(unsigned *arrive, unsigned target, int
             }
             __nanosleep(32);
         }
-        __threadfence();
         ok_sh = ok;
     }
     __syncthreads();
@@ -101,14 +105,25 @@ __device__ __forceinline__ void block_reduce(T (&acc)[ND], int nd, bool with_max
     __syncthreads();
 }
 
-// sum (or max) over the G block partials p[b * stride] by one warp, fixed order
+// sum (or max) over the G block partials p[b * stride] by one warp, fixed
+// order: lane l takes b = l, l + 32, ... in turn, then the warp combines the
+// lanes.  A lane issues the loads of 8 partials before it adds them, so their
+// L2 latencies overlap instead of adding up.
 template <class T>
 __device__ __forceinline__ T warp_sum_partials(const T *p, int G, int stride, bool is_max) {
+    constexpr int K = 8;
     const int lane = threadIdx.x & 31;
     T s = (T)0;
-    for (int b = lane; b < G; b += 32) {
-        const T v = __ldcg(p + (size_t)b * stride);
-        s = is_max ? fmax(s, v) : add_rn(s, v);
+    for (int b0 = lane; b0 < G; b0 += 32 * K) {
+        T v[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int b = b0 + 32 * k;
+            v[k] = (b < G) ? __ldcg(p + (size_t)b * stride) : (T)0;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (b0 + 32 * k < G) s = is_max ? fmax(s, v[k]) : add_rn(s, v[k]);
     }
     return is_max ? warp_max(s) : warp_sum(s);
 }

@@ -35,7 +35,11 @@ static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const 
             prof_begin(c, PK_RICH2, 0, s);
             const StagePlan pl = plan_stage(c, sizeof(TA), 0, 4);
             const StageCfg cfg{pl.stage_bytes, c.err};
-            if (pl.S == 3) {
+            if (pl.S == 3 && c.m_unit) {
+                auto kern = k_rich2_st<TA, VS, TC, TP, 3, true>;
+                launch_pdl(kern, dim3(rich_grid(c, kern, pl.smem)), dim3(kStagedThreads), pl.smem, s, S, val, rs, v, mv, out, par_misc, R, c.flags,
+                                                                          cd, n, cfg);
+            } else if (pl.S == 3) {
                 auto kern = k_rich2_st<TA, VS, TC, TP, 3>;
                 launch_pdl(kern, dim3(rich_grid(c, kern, pl.smem)), dim3(kStagedThreads), pl.smem, s, S, val, rs, v, mv, out, par_misc, R, c.flags,
                                                                           cd, n, cfg);

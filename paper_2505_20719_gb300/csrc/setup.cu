@@ -117,6 +117,12 @@ __global__ void k_fill(const int *rp, const int *ci, const double *val, int n, i
     }
 }
 
+// flag = 1 when some stored entry of M differs from 1
+template <class S> __global__ void k_m_nonunit(const S *m, int n, int *flag) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (!(to_c<double>(m[i]) == 1.0)) atomicOr(flag, 1);
+}
+
 // Factors of the approximate inverse M = (I - Dt^-1 U) Dt^-1 (I - L Dt^-1) of
 // A^ = L + D + U, Dt = alpha D: entry (i, c) of L Dt^-1 is A^_ic / dt_c
 // (c < i), of Dt^-1 U it is A^_ic / dt_i (c > i), both rounded to fp16 once
@@ -246,9 +252,24 @@ f3r_status build_matrix(Ctx &c, const int *rp, const int *ci, const double *val,
                                             c.ainv_u, c.ainv_dinv);
     }
     c.rowptr = (int *)dalloc(c, sizeof(int) * (n + 1));
-    if (!c.rowptr) return F3R_ERR_NOMEM;
+    int *nonunit = (int *)dalloc(c, sizeof(int));
+    if (!c.rowptr || !nonunit) return F3R_ERR_NOMEM;
     cudaMemcpyAsync(c.rowptr, rp, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s);
+    // M = I exactly (Jacobi of a matrix whose scaled diagonal is 1, or no M):
+    // the Richardson kernels then skip the loads of M; mul(1, v) = v, so the
+    // results are the same bits.
+    cudaMemsetAsync(nonunit, 0, sizeof(int), s);
+    switch (c.prm.m_prec) {
+        case F3R_F64: k_m_nonunit<<<gf, kBlock, 0, s>>>((const double *)c.mvec, n, nonunit); break;
+        case F3R_F32: k_m_nonunit<<<gf, kBlock, 0, s>>>((const float *)c.mvec, n, nonunit); break;
+        case F3R_F16: k_m_nonunit<<<gf, kBlock, 0, s>>>((const h16 *)c.mvec, n, nonunit); break;
+        default: k_m_nonunit<<<gf, kBlock, 0, s>>>((const b16 *)c.mvec, n, nonunit); break;
+    }
+    int nonunit_h = 1;
+    cudaMemcpyAsync(&nonunit_h, nonunit, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return F3R_ERR_CUDA;
+    const char *e = getenv("F3R_UNIT_M");  // 0: keep loading M (for the bit-identity test)
+    c.m_unit = (nonunit_h == 0) && !(e && e[0] == '0');
     return F3R_OK;
 }
 

@@ -55,6 +55,23 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         : "memory");
 }
 
+// L2 policy for data read once per pass (the matrix tiles): evicted first, so
+// that the vectors the next kernels read (the basis, w, z, x) stay in L2
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// bulk_g2s with an L2 cache policy
+__device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar,
+                                              uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+        : "memory");
+}
+
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -122,7 +139,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // owning slice s.  Every wait is bounded; a consumer that gives up records
 // the error and stops, the producer stops refilling after a failed wait and
 // finally waits (bounded) for the copies it issued.
-template <class TA, int S, class Body>
+template <class TA, int S, bool EVICT_FIRST = false, class Body>
 __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict__ val, int tile_begin,
                                              int tile_end, char *ring, int stage_bytes, uint64_t *full,
                                              uint64_t *empty, Extra ex, int *err, Body body) {
@@ -140,8 +157,14 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
         fence_proxy_async();  // the consumers' generic reads of this stage before the async refill
         mbar_expect_tx(bar, colb + valb + extb * ex.count);
         if (colb) {
-            bulk_g2s(dst, A.col + b0, colb, bar);
-            bulk_g2s(dst + colb, val + b0, valb, bar);
+            if constexpr (EVICT_FIRST) {
+                const uint64_t pol = l2_evict_first_policy();
+                bulk_g2s_hint(dst, A.col + b0, colb, bar, pol);
+                bulk_g2s_hint(dst + colb, val + b0, valb, bar, pol);
+            } else {
+                bulk_g2s(dst, A.col + b0, colb, bar);
+                bulk_g2s(dst + colb, val + b0, valb, bar);
+            }
         }
         for (int l = 0; l < ex.count; ++l)
             bulk_g2s(dst + colb + valb + l * extb,

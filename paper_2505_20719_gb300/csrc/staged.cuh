@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const T
     ex.ld = L.ld;
     ex.esize = sizeof(T);
     const int2 tr = tile_range(A);
-    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), ex, cfg.err,
+    staged_tiles<TA, S, true>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), ex, cfg.err,
                         [&](int s, const StageView<TA> &v) {
                              T y = staged_row<T>(v, lane, [&](int c) { return __ldg(x + c); });
                              const int i = s * kSlice + lane;
@@ -99,8 +99,9 @@ __global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const T
     });
 }
 
-// fused plain Richardson call with m4 = 2 (see k_rich2)
-template <class TA, class VS, class TC, class TP, int S>
+// fused plain Richardson call with m4 = 2 (see k_rich2).  UNIT: every entry
+// of M is 1, so M v is v itself (mul(1, v) = v) and M is not loaded.
+template <class TA, class VS, class TC, class TP, int S, bool UNIT = false>
 __global__ void __launch_bounds__(kStagedThreads) k_rich2_st(Sell A, const TA *__restrict__ val, const float *__restrict__ rs,
                                                      const VS *__restrict__ v, const VS *__restrict__ mv, TP *out,
                                                      const TP *par_misc, RichDev<TC> R, const int *flags,
@@ -115,16 +116,16 @@ __global__ void __launch_bounds__(kStagedThreads) k_rich2_st(Sell A, const TA *_
     staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), Extra(), cfg.err,
                         [&](int s, const StageView<TA> &st) {
                              TC acc = staged_row<TC>(st, lane, [&](int c) {
-                                 return rnd<VS>(fma_rn(w1, mul_rn(to_c<TC>(__ldg(mv + c)), to_c<TC>(__ldg(v + c))),
-                                                       (TC)0));
+                                 const TC vc = to_c<TC>(__ldg(v + c));
+                                 return rnd<VS>(fma_rn(w1, UNIT ? vc : mul_rn(to_c<TC>(__ldg(mv + c)), vc), (TC)0));
                              });
                              const int i = s * kSlice + lane;
                              if (rs) acc = mul_rn(acc, (TC)__ldg(rs + i));
                              if (i < n) {
-                                 const TC vi = to_c<TC>(v[i]), mi = to_c<TC>(mv[i]);
-                                 const TC z1 = rnd<VS>(fma_rn(w1, mul_rn(mi, vi), (TC)0));
+                                 const TC vi = to_c<TC>(v[i]);
+                                 const TC z1 = rnd<VS>(fma_rn(w1, UNIT ? vi : mul_rn(to_c<TC>(mv[i]), vi), (TC)0));
                                  const TC ri = rnd<VS>(sub_rn(vi, acc));
-                                 const TC z2 = rnd<VS>(fma_rn(w2, mul_rn(mi, ri), z1));
+                                 const TC z2 = rnd<VS>(fma_rn(w2, UNIT ? ri : mul_rn(to_c<TC>(mv[i]), ri), z1));
                                  out[i] = mul_rn((TP)z2, inv_sigma);
                              }
                          });

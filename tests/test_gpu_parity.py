@@ -401,3 +401,23 @@ def test_graphs_and_direct_launches_agree():
         r = s.solve(np.ascontiguousarray(prob.b), x)
         out.append((x, r.outer_iters))
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_unit_jacobi_richardson_bit_identical(monkeypatch):
+    """Under symmetric diagonal scaling the stored Jacobi M is exactly 1 and the
+    Richardson kernels skip its loads (M v = v).  The solve must be the same,
+    bit for bit, as with the general kernels (F3R_UNIT_M=0 at set-up)."""
+    prob = G.diffusion3d_7pt(dims=(40, 36, 30), seed=109)
+    out = []
+    for unit in ("1", "0"):
+        monkeypatch.setenv("F3R_UNIT_M", unit)
+        s = solver(prob, f3r.default_params())
+        monkeypatch.delenv("F3R_UNIT_M")
+        assert np.all(s.export(6) == np.uint16(0x3C00))
+        x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+        r = s.solve(dev(prob.b), x)
+        torch.cuda.synchronize()
+        out.append((x.cpu().numpy(), r.outer_iters, np.array(r.hist)))
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][2], out[1][2])
