@@ -100,6 +100,30 @@ template <class T> struct GridRed {
     int stride;
 };
 
+// Block totals of nd sums (warps summed in order) written to
+// part[d * gridDim.x + blockIdx.x]; the next kernel sums them over blocks
+// (warp_sum_partials), so no block waits for a last one here.
+template <class T, int ND>
+__device__ __forceinline__ void block_partials(T (&acc)[ND], int nd, T *part) {
+    __shared__ T sm[ND][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+        if (d < nd) {
+            const T v = warp_sum(acc[d]);
+            if (lane == 0) sm[d][warp] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nd) {
+        const int d = threadIdx.x;
+        T s = sm[d][0];
+        for (int w = 1; w < nwarps; ++w) s = add_rn(s, sm[d][w]);
+        part[(size_t)d * gridDim.x + blockIdx.x] = s;
+    }
+}
+
 // Deterministic grid-wide reduction of `nd` sums (and optionally one max,
 // passed as acc[nd] when with_max) per thread.  Every block writes its
 // partials; the last block to arrive (atomic ticket) sums all partials in a

@@ -95,6 +95,8 @@ struct Ctx {
     void *partials = nullptr;
     unsigned *ticket = nullptr;
     unsigned *coop = nullptr;   // grid-barrier counters of cooperative launches (zero between launches)
+    void *hpart = nullptr;      // [l][block] totals of hA left by the SpMV + dots for the fused CGS2
+    int hpart_G[4] = {0, 0, 0, 0};  // blocks of that SpMV per level (0: it reduced hA itself)
     FusedPlan fplan[4];
     StepPlan stplan;
     int stplan_bps = 0;         // blocks per SM the step plan is being tried with

@@ -80,6 +80,8 @@ template <class T> struct FusedScratch {
     unsigned *bar;  // arrivals, exits (zero between launches)
     int *err;
     int chunk;      // rows per block (multiple of kFusedChunkAlign)
+    const T *hpart; // [l][hG] block totals of hA from the SpMV + dots (null: hA is in the scalars)
+    int hG;
 };
 
 // block-wide sums of acc[0..nd) (and a max in acc[nd] when with_max) in warp
@@ -146,9 +148,26 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8) ? 2 : 1)
     const T *__restrict__ w = L.w + r0;
     bool ok = true;
 
+    // hA: the sum of the SpMV's block totals (every block alike; block 0 keeps
+    // it for the Givens step), or the value a grid reduction left
+    auto load_hA = [&]() {
+        if (fs.hpart) {
+            const int warp = threadIdx.x >> 5;
+            for (int l = warp; l <= j; l += kFusedWarps) {
+                const T sm = warp_sum_partials(fs.hpart + (size_t)l * fs.hG, fs.hG, 1, false);
+                if ((threadIdx.x & 31) == 0) {
+                    hs[l] = sm;
+                    if (blockIdx.x == 0) L.hA()[l] = sm;
+                }
+            }
+        } else if (threadIdx.x <= j) {
+            hs[threadIdx.x] = L.hA()[threadIdx.x];
+        }
+    };
+
     // ---- phase A: w1 = w - V hA, partial hB
     if (passes == 2) {
-        if (threadIdx.x <= j) hs[threadIdx.x] = L.hA()[threadIdx.x];
+        load_hA();
         __syncthreads();
         T acc[MAXD];
 #pragma unroll
@@ -200,7 +219,7 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8) ? 2 : 1)
             __syncthreads();
         }
     } else {
-        if (threadIdx.x <= j) hs[threadIdx.x] = L.hA()[threadIdx.x];
+        load_hA();
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) ws[i] = w[i];
         __syncthreads();
     }

@@ -97,7 +97,7 @@ bool fused_go(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_t s, boo
     } else if (CHILD == CHILD_R) {
         co.x = (TC *)c.rin;
     }
-    FusedScratch<T> fs{(T *)c.partials, c.coop, c.err, p.chunk};
+    FusedScratch<T> fs{(T *)c.partials, c.coop, c.err, p.chunk, c.hpart_G[d] ? (const T *)c.hpart : nullptr, c.hpart_G[d]};
     GridRed<TC> grc{(TC *)c.partials, c.ticket, kMaxDots};
     return launch_coop(kern, dim3(p.G), dim3(kFusedThreads), p.smem, s, levdev_inner<T>(c, d), j,
                        c.prm.cgs_passes, last ? 1 : 0, want_sigma_of(c, d), do_norm ? 1 : 0, co, fs, grc) ==

@@ -146,8 +146,11 @@ static void spmv_dots_st_go(Ctx &c, int d, int j, const TA *val, const float *rs
                             cudaStream_t s) {
     auto kern = k_spmv_dots_st<TA, T, S, MAXD>;
     const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
+    // block totals of hA for the fused CGS2 launch that follows, when it will run
+    const bool defer = d >= 1 && d <= 3 && c.fplan[d].G > 0;
+    c.hpart_G[d] = defer ? g : 0;
     launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots),
-                                    StageCfg{pl.stage_bytes, c.err});
+                                    StageCfg{pl.stage_bytes, c.err}, defer ? (T *)c.hpart : (T *)nullptr);
 }
 
 template <class TA, class T>
@@ -163,6 +166,7 @@ static void spmv_dots_go(Ctx &c, int d, int j, const TA *val, const float *rs, c
         else if (md == 8) spmv_dots_st_go<TA, T, 2, 8>(c, d, j, val, rs, pl, s);
         else spmv_dots_st_go<TA, T, 2, 16>(c, d, j, val, rs, pl, s);
     } else {
+        c.hpart_G[d] = 0;
         launch_pdl(k_spmv_dots<TA, T>, dim3(c.Gs), dim3(kBlock), 0, s, sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots));
     }
 }

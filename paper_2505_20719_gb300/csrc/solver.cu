@@ -433,6 +433,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
                                     (size_t)(kMaxOuterM + 2) * c.G1 * sizeof(double),
                                     (size_t)(2 * (kMaxOuterM + 1) + 2) * c.nsm * 2 * sizeof(double)});
     c.partials = dalloc(c, pbytes);
+    c.hpart = dalloc(c, (size_t)c.nsm * 8 * kMaxDots * sizeof(double));
     c.ticket = (unsigned *)dalloc(c, sizeof(unsigned) * 4);
     c.coop = (unsigned *)dalloc(c, sizeof(unsigned) * 4);
     c.err = (int *)dalloc(c, sizeof(int) * 4);
@@ -440,7 +441,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     c.jdev = (int *)dalloc(c, sizeof(int) * 4);
     h->rb_dev = (Readback *)dalloc(c, sizeof(Readback));
     if (!c.omega || !c.wcur || !c.counters || !c.c_ntr_base || !c.zst || !c.apply_misc || !c.partials ||
-        !c.ticket || !c.coop || !c.err || !c.flags || !c.jdev || !h->rb_dev)
+        !c.hpart || !c.ticket || !c.coop || !c.err || !c.flags || !c.jdev || !h->rb_dev)
         return fail(F3R_ERR_NOMEM);
     plan_cgs_fused(c);
     if (cudaHostAlloc((void **)&c.rb, sizeof(Readback), cudaHostAllocDefault) != cudaSuccess ||

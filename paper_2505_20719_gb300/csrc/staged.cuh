@@ -62,11 +62,14 @@ __device__ __forceinline__ TC staged_row(const StageView<TA> &v, int lane, GX gx
     return acc;
 }
 
-// w = A Z[j] (times the row scale), hA = V[0..j]^T w; V rows staged with the slice
+// w = A Z[j] (times the row scale), hA = V[0..j]^T w; V rows staged with the
+// slice.  hpart != null: the block totals of hA go to hpart[l * grid + block]
+// for the fused CGS2 launch that follows to sum; else a grid reduction
+// leaves hA itself in the level's scalars.
 template <class TA, class T, int S, int MAXD>
 __global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const TA *__restrict__ val,
                                                          const float *__restrict__ rs, LevelDev<T> L, int j,
-                                                         GridRed<T> gr, StageCfg cfg) {
+                                                         GridRed<T> gr, StageCfg cfg, T *hpart) {
     pdl_enter();
     if (stopped(L.flags, L.depth)) return;
     extern __shared__ __align__(128) char dsm[];
@@ -93,6 +96,10 @@ __global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const T
                                      if (l <= j) acc[l] = fma_rn(v.template ext<T>(l)[lane], y, acc[l]);
                              }
                          });
+    if (hpart) {
+        block_partials<T, MAXD>(acc, j + 1, hpart);
+        return;
+    }
     grid_reduce<T, MAXD>(acc, j + 1, false, gr, [&](T *res) {
         T *hA = L.hA();
         for (int l = 0; l <= j; ++l) hA[l] = res[l];
