@@ -436,8 +436,10 @@ __global__ void __launch_bounds__(kVecBlock) k_normalize(LevelDev<T> L, const T 
 
 // z = sum_{k < kdim} y_k Z[k] (fma in k order) into the parent's slot, times
 // D^-1/2 when returning to level 0.  A level whose input was non-finite
-// returns NaN so that the outer level notices.
-template <class T, class TP>
+// returns NaN so that the outer level notices.  A thread loads its pack of
+// every Z[k] (k < kdim <= MAXD) before the first fma, so the kdim loads are
+// in flight together.
+template <class T, class TP, int MAXD>
 __global__ void __launch_bounds__(kVecBlock) k_combine(LevelDev<T> L, TP *out_base, const int *out_j, int out_ld,
                                                        const double *dsc) {
     pdl_enter();
@@ -453,32 +455,23 @@ __global__ void __launch_bounds__(kVecBlock) k_combine(LevelDev<T> L, TP *out_ba
     auto one = [&](int i, T s) { out[i] = dsc ? (TP)mul_rn(dsc[i], (double)s) : (TP)s; };
     const bool vec = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && ((sizeof(TP) * N) % 16 == 0 || sizeof(TP) >= sizeof(T));
     const int nq = vec ? L.n / N : 0;
-    for_packs(nq, [&](int q0, int nthr) {
-        Pack<T, N> sum[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-#pragma unroll
-            for (int e = 0; e < N; ++e) sum[u].v[e] = (T)0;
-        for (int l = 0; l < k; ++l) {
-            Pack<T, N> zl[kUnroll];
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (q0 + u * nthr < nq) zl[u] = ldp<T, N>(L.Z + (size_t)l * L.ld + (size_t)(q0 + u * nthr) * N);
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u)
-                if (q0 + u * nthr < nq)
-#pragma unroll
-                    for (int e = 0; e < N; ++e) sum[u].v[e] = fma_rn(ys[l], zl[u].v[e], sum[u].v[e]);
-        }
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int q = q0 + u * nthr;
-            if (q < nq)
-#pragma unroll
-                for (int e = 0; e < N; ++e) one(q * N + e, nonfinite ? (T)NAN : sum[u].v[e]);
-        }
-    });
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int q = tid; q < nq; q += nth) {
+        Pack<T, N> zl[MAXD];
+#pragma unroll
+        for (int l = 0; l < MAXD; ++l)
+            if (l < k) zl[l] = ldp<T, N>(L.Z + (size_t)l * L.ld + (size_t)q * N);
+        Pack<T, N> sum;
+#pragma unroll
+        for (int e = 0; e < N; ++e) sum.v[e] = (T)0;
+#pragma unroll
+        for (int l = 0; l < MAXD; ++l)
+            if (l < k)
+#pragma unroll
+                for (int e = 0; e < N; ++e) sum.v[e] = fma_rn(ys[l], zl[l].v[e], sum.v[e]);
+#pragma unroll
+        for (int e = 0; e < N; ++e) one(q * N + e, nonfinite ? (T)NAN : sum.v[e]);
+    }
     for (int i = nq * N + tid; i < L.n; i += nth) {
         T s = (T)0;
         for (int l = 0; l < k; ++l) s = fma_rn(ys[l], L.Z[(size_t)l * L.ld + i], s);

@@ -222,7 +222,9 @@ void launch_cgs_final(Ctx &c, int d, int j, bool last, cudaStream_t s) {
 template <class T, class TP>
 static void comb_go(Ctx &c, int d, const OutSlot &o, cudaStream_t s) {
     prof_begin(c, PK_COMBINE, d, s);
-    launch_pdl(k_combine<T, TP>, dim3(c.Gv), dim3(kVecBlock), 0, s, levdev<T>(c, d), (TP *)o.ptr, nullptr, 0, o.dscale ? c.dsc : nullptr);
+    const int md = maxd_bucket(c.L[d].m);
+    auto kern = (md == 4) ? k_combine<T, TP, 4> : (md == 8) ? k_combine<T, TP, 8> : k_combine<T, TP, 16>;
+    launch_pdl(kern, dim3(c.Gv), dim3(kVecBlock), 0, s, levdev<T>(c, d), (TP *)o.ptr, nullptr, 0, o.dscale ? c.dsc : nullptr);
     prof_end(c, s);
     c.launches++;
 }
