@@ -110,6 +110,9 @@ struct Extra {
 
 constexpr int kTileSlices = kWarps;              // one slice per warp of the block
 constexpr int kTileRows = kTileSlices * kSlice;  // 256 rows per tile
+// stage header: the tile's kTileSlices + 1 slice offsets (int), padded to a
+// multiple of 16 bytes so the bulk copies after it stay aligned
+constexpr int kStageHdr = ((kTileSlices + 1) * 4 + 15) / 16 * 16;
 
 // What one warp sees of its slice in a staged tile.
 template <class TA> struct StageView {
@@ -145,15 +148,26 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
                                              uint64_t *empty, Extra ex, int *err, Body body) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool producer = (warp == kWarps);
+    // run by the whole producer warp: lanes 0..8 write the tile's slice
+    // offsets into the stage header (the consumers read them from shared
+    // memory instead of global memory), lane 0 issues the bulk copies
     auto issue = [&](int t, int st) {
         const int s0 = t * kTileSlices;
         const int s1 = min(s0 + kTileSlices, A.nslices);
-        const int b0 = __ldg(A.sptr + s0), b1 = __ldg(A.sptr + s1);
+        char *sbase = ring + (size_t)st * stage_bytes;
+        int off = 0;
+        if (lane <= kTileSlices) {
+            off = __ldg(A.sptr + min(s0 + lane, s1));
+            reinterpret_cast<int *>(sbase)[lane] = off;
+        }
+        const int b0 = __shfl_sync(0xffffffffu, off, 0), b1 = __shfl_sync(0xffffffffu, off, kTileSlices);
+        __syncwarp();  // the header before lane 0's arrive (release) on full[st]
+        if (lane != 0) return;
         const uint32_t colb = (uint32_t)(b1 - b0) * 4u;
         const uint32_t valb = (uint32_t)(b1 - b0) * (uint32_t)sizeof(TA);
         const uint32_t extb = (uint32_t)kTileRows * ex.esize;
         const uint32_t bar = smem_u32(full + st);
-        const uint32_t dst = smem_u32(ring + (size_t)st * stage_bytes);
+        const uint32_t dst = smem_u32(sbase + kStageHdr);
         fence_proxy_async();  // the consumers' generic reads of this stage before the async refill
         mbar_expect_tx(bar, colb + valb + extb * ex.count);
         if (colb) {
@@ -188,7 +202,7 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
                 ok = false;
                 break;
             }
-            if (lane == 0) issue(t, st);
+            issue(t, st);
             __syncwarp();
         }
         // wait for the copies of the last (up to S) tiles issued, so none lands after exit
@@ -208,14 +222,16 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
             const int s = t * kTileSlices + warp;
             if (s < A.nslices) {
                 const char *base = ring + (size_t)st * stage_bytes;
-                const int bt = __ldg(A.sptr + t * kTileSlices);
-                const int tile_nnz = __ldg(A.sptr + min(t * kTileSlices + kTileSlices, A.nslices)) - bt;
-                const int b0 = __ldg(A.sptr + s), b1 = __ldg(A.sptr + s + 1);
+                const int *hdr = reinterpret_cast<const int *>(base);
+                const int bt = hdr[0];
+                const int tile_nnz = hdr[kTileSlices] - bt;
+                const int b0 = hdr[warp], b1 = hdr[warp + 1];
+                const char *body_base = base + kStageHdr;
                 StageView<TA> v;
                 v.w = (b1 - b0) >> 5;
-                v.col = reinterpret_cast<const int *>(base) + (b0 - bt);
-                v.val = reinterpret_cast<const TA *>(base + (size_t)tile_nnz * 4) + (b0 - bt);
-                v.extra = base + (size_t)tile_nnz * (4 + sizeof(TA));
+                v.col = reinterpret_cast<const int *>(body_base) + (b0 - bt);
+                v.val = reinterpret_cast<const TA *>(body_base + (size_t)tile_nnz * 4) + (b0 - bt);
+                v.extra = body_base + (size_t)tile_nnz * (4 + sizeof(TA));
                 v.esize = ex.esize;
                 v.row0 = warp * kSlice;
                 body(s, v);
@@ -229,7 +245,7 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
 
 // stage size in bytes for tiles of slices up to wmax wide
 __host__ __device__ inline int stage_bytes_for(int wmax, int asize, int n_extra, int esize) {
-    const int b = kTileSlices * wmax * kSlice * (4 + asize) + n_extra * kTileRows * esize;
+    const int b = kStageHdr + kTileSlices * wmax * kSlice * (4 + asize) + n_extra * kTileRows * esize;
     return (b + 15) / 16 * 16;
 }
 
