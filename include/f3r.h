@@ -324,7 +324,13 @@ f3r_status f3r_residual_noalloc(int32_t n, const int32_t *rowptr, const int32_t 
 /* Device memory held by the context, in bytes. */
 int64_t f3r_device_bytes(const f3r_ctx *ctx);
 
+/* Releases the context (its buffers return to the library's per-device memory
+ * pool, which keeps them for later contexts of this process). */
 void f3r_destroy(f3r_ctx *ctx);
+
+/* Returns the device memory that the library's pools keep but no context uses
+ * to the driver.  Contexts' own buffers are not touched. */
+f3r_status f3r_trim_memory(void);
 const char *f3r_status_str(f3r_status s);
 
 #ifdef __cplusplus

@@ -763,6 +763,7 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
         b->sys.push_back(c);
         c->dev = dev;
         c->nsm = nsm;
+        c->zstream = s;  // the copies of A are allocated and built in the batch's stream
         c->prm = prm;
         c->n = d.n;
         c->nnz = d.nnz;
@@ -976,11 +977,14 @@ int64_t f3r_batched_device_bytes(const f3r_batch *b) {
 void f3r_destroy_batched(f3r_batch *b) {
     if (!b) return;
     for (Ctx *c : b->sys) {
-        for (void *p : c->allocs) cudaFree(p);
+        for (void *p : c->allocs) pool_free(p, b->cs);
         delete c;
     }
     for (void *p : b->allocs) cudaFree(p);
-    if (b->cs) cudaStreamDestroy(b->cs);
+    if (b->cs) {
+        cudaStreamSynchronize(b->cs);
+        cudaStreamDestroy(b->cs);
+    }
     delete b;
 }
 

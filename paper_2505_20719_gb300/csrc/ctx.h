@@ -214,6 +214,9 @@ struct StagePlan {
     int S = 0, stage_bytes = 0, smem = 0;
 };
 StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize);
+// stream-ordered device memory from the per-device pool (mem.cu)
+void *pool_alloc(int dev, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
 int maxd_bucket(int m);
 
 }  // namespace f3r

@@ -544,11 +544,11 @@ struct LearnedState {
 
 namespace {
 void *lalloc(Ctx &c, size_t bytes) {
-    void *p = nullptr;
-    if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+    void *p = pool_alloc(c.dev, bytes, c.zstream);
+    if (!p) return nullptr;
     c.allocs.push_back(p);
     c.bytes += (long long)bytes;
-    cudaMemset(p, 0, bytes);
+    cudaMemsetAsync(p, 0, bytes, c.zstream);
     return p;
 }
 
@@ -601,6 +601,9 @@ f3r_status learned_enable(Ctx &c, const float *theta_host_or_dev, bool train) {
         if (!L.dP[0] || !L.dP[1] || !L.U || !L.dHs) return F3R_ERR_NOMEM;
         L.train_buffers = true;
     }
+    // the buffers are allocated and zeroed in the context's stream; the
+    // copies below run in the legacy stream
+    if (cudaStreamSynchronize(c.zstream) != cudaSuccess) return F3R_ERR_CUDA;
     if (theta_host_or_dev) {
         cudaMemcpy(L.theta, theta_host_or_dev, sizeof(float) * lm::kNP, cudaMemcpyDefault);
         cudaMemset(L.am, 0, sizeof(float) * lm::kNP);

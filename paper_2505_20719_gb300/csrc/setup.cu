@@ -173,9 +173,9 @@ __global__ void k_export(const int *rp, int n, const int *sptr, const S *src, S 
 }
 
 static void *dalloc(Ctx &c, size_t bytes) {
-    void *p = nullptr;
     if (bytes == 0) bytes = 16;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    void *p = pool_alloc(c.dev, bytes, c.zstream);
+    if (!p) return nullptr;
     c.allocs.push_back(p);
     c.bytes += (long long)bytes;
     return p;

@@ -40,9 +40,9 @@ bool is_device_ptr(const void *p) {
 // device allocation, zero-filled in the context's stream (so the fill is
 // ordered before every later use in that stream, unlike a legacy-stream memset)
 void *dalloc(Ctx &c, size_t bytes) {
-    void *p = nullptr;
     if (bytes == 0) bytes = 16;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+    void *p = pool_alloc(c.dev, bytes, c.zstream);
+    if (!p) return nullptr;
     c.allocs.push_back(p);
     c.bytes += (long long)bytes;
     cudaMemsetAsync(p, 0, bytes, c.zstream);
@@ -319,7 +319,8 @@ void f3r_destroy(f3r_ctx *h) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
-    for (void *p : c.allocs) cudaFree(p);
+    for (void *p : c.allocs) pool_free(p, c.zstream);
+    if (c.zstream) cudaStreamSynchronize(c.zstream);
     if (c.rb) cudaFreeHost(c.rb);
     if (c.hostval) cudaFreeHost(c.hostval);
     if (c.ev0) cudaEventDestroy(c.ev0);
@@ -373,7 +374,8 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     void *tmp[3] = {nullptr, nullptr, nullptr};
     auto up = [&](const void *src, size_t bytes, int slot) -> const void * {
         if (is_device_ptr(src)) return src;
-        if (cudaMalloc(&tmp[slot], bytes ? bytes : 16) != cudaSuccess) return nullptr;
+        tmp[slot] = pool_alloc(dev, bytes, s);
+        if (!tmp[slot]) return nullptr;
         cudaMemcpyAsync(tmp[slot], src, bytes, cudaMemcpyHostToDevice, s);
         return tmp[slot];
     };
@@ -382,7 +384,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     va = (const double *)up(val, sizeof(double) * (size_t)nnz, 2);
     auto fail = [&](f3r_status e) {
         for (void *p : tmp)
-            if (p) cudaFree(p);
+            if (p) pool_free(p, s);
         f3r_destroy(h);
         return e;
     };
@@ -390,7 +392,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     st = build_matrix(c, rp, ci, va, s);
     if (st != F3R_OK) return fail(st);
     for (void *p : tmp)
-        if (p) cudaFree(p);
+        if (p) pool_free(p, s);
     tmp[0] = tmp[1] = tmp[2] = nullptr;
 
     // grid shapes: a few resident blocks per SM, never more blocks than work

@@ -86,6 +86,7 @@ def lib():
         L.f3r_device_bytes.argtypes = [vp]
         L.f3r_device_bytes.restype = C.c_int64
         L.f3r_destroy.argtypes = [vp]
+        L.f3r_trim_memory.argtypes = []
         L.f3r_status_str.restype = C.c_char_p
         L.f3r_profile_enable.argtypes = [vp, C.c_int]
         L.f3r_profile_enable.restype = C.c_int
@@ -160,6 +161,11 @@ def _set(p, kw):
         else:
             setattr(p, k, v)
     return p
+
+
+def trim_memory():
+    """Return the device memory the library's pools keep for later contexts."""
+    _check(lib().f3r_trim_memory(), "f3r_trim_memory")
 
 
 def default_params(**kw) -> Params:

@@ -421,3 +421,23 @@ def test_unit_jacobi_richardson_bit_identical(monkeypatch):
     assert out[0][1] == out[1][1]
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][2], out[1][2])
+
+
+def test_pooled_context_memory_reused_and_trimmed():
+    """Contexts take their buffers from the library's device pool: a context
+    set up on memory an earlier one released solves bit for bit alike, and
+    trimming the pool afterwards succeeds."""
+    prob = G.diffusion3d_7pt(dims=(20, 18, 16), seed=110)
+    out = []
+    for _ in range(2):
+        s = solver(prob, f3r.default_params())
+        x = np.zeros(prob.n)
+        r = s.solve(np.ascontiguousarray(prob.b), x)
+        s.close()
+        out.append((x, r.outer_iters))
+    f3r.trim_memory()
+    assert out[0][1] == out[1][1] and np.array_equal(out[0][0], out[1][0])
+    s = solver(prob, f3r.default_params())
+    x = np.zeros(prob.n)
+    assert s.solve(np.ascontiguousarray(prob.b), x).outer_iters == out[0][1]
+    assert np.array_equal(x, out[0][0])
