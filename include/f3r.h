@@ -96,7 +96,11 @@ typedef struct {
                            cooperative launch when the default precision schedule, Jacobi M
                            and m4 = 2 apply; 0 (default): separate launches, which measured
                            as fast inside CUDA graphs with more blocks per SM */
-    int reserved[3];
+    int batch_split;    /* f3r_setup_batched only: systems of at least this many rows are solved
+                           one after another by the single-system path (the whole GPU each),
+                           the others in the one persistent launch; 0 (default): 2048 rows per
+                           SM of the device; < 0: every system in the persistent launch */
+    int reserved[2];
 } f3r_params;
 
 typedef struct {
@@ -238,14 +242,18 @@ f3r_status f3r_solve_krylov(f3r_ctx *ctx, int method, const double *b, double *x
                             f3r_stats *stats, void *stream);
 
 /* ---------------------------------------------------------------- batched
- * Many systems, each with one or more right-hand sides, solved by F3R in a
- * single persistent kernel launch (project addition; the paper solves one
- * system at a time).  Each (system, right-hand side) instance is solved
- * entirely on the device by one thread-block cluster with the default F3R
- * precision schedule (Table 1): fp64 FGMRES(m1) with its convergence test
- * and restarts, fp32 FGMRES(m2), FGMRES(m3) with fp16 A, fp16 Richardson
- * R_2 with adaptive weights (Algorithm 1), Jacobi M.  Clusters take instances
- * largest-first from an atomic work queue. */
+ * Many systems, each with one or more right-hand sides, solved by F3R
+ * (project addition; the paper solves one system at a time).  Each
+ * (system, right-hand side) instance of a small system is solved entirely on
+ * the device by one thread-block cluster of a single persistent kernel
+ * launch with the default F3R precision schedule (Table 1): fp64
+ * FGMRES(m1) with its convergence test and restarts, fp32 FGMRES(m2),
+ * FGMRES(m3) with fp16 A, fp16 Richardson R_2 with adaptive weights
+ * (Algorithm 1), Jacobi M.  Clusters take instances largest-first from an
+ * atomic work queue.  Systems of at least params.batch_split rows are set up
+ * as single-system contexts and their instances solved one after another
+ * (the whole GPU each) before the persistent launch: on one cluster they
+ * would keep the launch waiting long after the other clusters finished. */
 typedef struct f3r_batch f3r_batch;
 
 typedef struct {
@@ -264,7 +272,8 @@ typedef struct {
     double rel_res_true;     /* final ||b - A x|| / ||b|| */
     int64_t m_applies;
     int64_t r_calls;
-    double t_solve_ms;       /* device time of the whole batched launch */
+    double t_solve_ms;       /* device time of the whole persistent launch, or of the
+                                instance's own solve (systems of >= batch_split rows) */
     int system, rhs;         /* which instance */
 } f3r_batch_result;
 
@@ -278,8 +287,9 @@ f3r_status f3r_setup_batched(f3r_batch **batch, int nsys, const f3r_system_desc 
 
 /* Solve every instance: B[q] and X[q] are device pointers (n of system q's
  * system fp64 values) for instance q, instances numbered system by system
- * and right-hand side by right-hand side; X[q] holds x0 on entry.  One
- * kernel launch; res (optional, one entry per instance) receives each
+ * and right-hand side by right-hand side; X[q] holds x0 on entry.  The
+ * instances of large systems first (f3r_solve each), then one kernel launch
+ * for the rest; res (optional, one entry per instance) receives each
  * instance's result.  Returns F3R_OK if every instance converged, else the
  * status of the first instance that did not. */
 f3r_status f3r_solve_batched(f3r_batch *batch, const double *const *B, double *const *X, f3r_batch_result *res,
@@ -287,7 +297,7 @@ f3r_status f3r_solve_batched(f3r_batch *batch, const double *const *B, double *c
 
 /* Thread-block cluster size of the batched launch (1, 2, 4 or 8; default 8). */
 f3r_status f3r_batched_set_cluster(f3r_batch *batch, int cluster_size);
-/* Autotuner: times one outer iteration of the whole batch (from x0 = 0) for
+/* Autotuner: times one outer iteration of the persistent launch's instances (from x0 = 0) for
  * cluster sizes 1, 2, 4 and 8 and keeps the fastest (written to *chosen if
  * not NULL).  B and X as in f3r_solve_batched; X is zero on return. */
 f3r_status f3r_batched_autotune(f3r_batch *batch, const double *const *B, double *const *X, int *chosen,

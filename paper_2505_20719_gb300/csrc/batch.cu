@@ -44,6 +44,7 @@ struct Sys {
     const h16 *a16;      // A^ fp16
     const double *dsc;   // D^-1/2
     const h16 *m16;      // Jacobi M
+    int m_unit;          // every entry of M is exactly 1: M v = v, M is not loaded
 };
 
 struct Inst {
@@ -243,15 +244,17 @@ __device__ void rich_call(Ctx2 &C, float inv_sigma, float *out) {
     if (!update) {
         const float w1 = sh.omega[0], w2 = sh.omega[1];
         for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
+            const bool unit = S.m_unit != 0;
             const float acc = row_sum<float>(S, S.a16, s, tm.lane, [&](int c) {
-                return rnd<h16>(fma_rn(w1, mul_rn(to_c<float>(__ldg(S.m16 + c)), to_c<float>(ldcg(I.rin + c))), 0.0f));
+                const float vc = to_c<float>(ldcg(I.rin + c));
+                return rnd<h16>(fma_rn(w1, unit ? vc : mul_rn(to_c<float>(__ldg(S.m16 + c)), vc), 0.0f));
             });
             const int i = s * kSlice + tm.lane;
             if (i < n) {
-                const float vi = to_c<float>(ldcg(I.rin + i)), mi = to_c<float>(__ldg(S.m16 + i));
-                const float z1 = rnd<h16>(fma_rn(w1, mul_rn(mi, vi), 0.0f));
+                const float vi = to_c<float>(ldcg(I.rin + i));
+                const float z1 = rnd<h16>(fma_rn(w1, unit ? vi : mul_rn(to_c<float>(__ldg(S.m16 + i)), vi), 0.0f));
                 const float ri = rnd<h16>(sub_rn(vi, acc));
-                const float z2 = rnd<h16>(fma_rn(w2, mul_rn(mi, ri), z1));
+                const float z2 = rnd<h16>(fma_rn(w2, unit ? ri : mul_rn(to_c<float>(__ldg(S.m16 + i)), ri), z1));
                 out[i] = mul_rn(z2, inv_sigma);
             }
         }
@@ -694,7 +697,9 @@ __global__ void __launch_bounds__(kBT) k_batch(const Sys *sys, const Inst *inst,
 using namespace f3r;
 
 struct f3r_batch {
-    std::vector<Ctx *> sys;   // matrix of each system (set-up arrays only)
+    std::vector<Ctx *> sys;   // matrix of each system (set-up arrays only; none for a large system)
+    std::vector<f3r_ctx *> full;  // large systems: a single-system context, else null
+    std::vector<int> small;   // instances of the persistent launch, largest first
     std::vector<int> nrhs;
     std::vector<int> inst_sys, inst_rhs;
     bt::BP P{};
@@ -754,6 +759,12 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // systems of at least `split` rows are solved one after another by the
+    // single-system path (the whole GPU each); in the persistent launch they
+    // would run on one cluster and keep the launch waiting on them
+    const long long split = prm.batch_split > 0 ? (long long)prm.batch_split
+                                                : (prm.batch_split < 0 ? (1LL << 40) : 2048LL * nsm);
+    b->full.assign(nsys, nullptr);
     std::vector<bt::Sys> hs(nsys);
     for (int k = 0; k < nsys; ++k) {
         const f3r_system_desc &d = desc[k];
@@ -768,6 +779,18 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
         c->n = d.n;
         c->nnz = d.nnz;
         c->ld = (int)(((long long)d.n + 255) / 256 * 256);
+        if (d.n >= split) {
+            const f3r_status st = f3r_setup(&b->full[k], d.n, d.nnz, d.rowptr, d.colidx, d.val, &prm, (void *)s);
+            if (st != F3R_OK) return fail(st);
+            hs[k] = bt::Sys{};
+            hs[k].n = d.n;
+            for (int r = 0; r < d.nrhs; ++r) {
+                b->inst_sys.push_back(k);
+                b->inst_rhs.push_back(r);
+            }
+            b->nrhs.push_back(d.nrhs);
+            continue;
+        }
         // upload the CSR arrays (host or device) and build the copies of A
         void *tmp[3] = {nullptr, nullptr, nullptr};
         const size_t sz[3] = {sizeof(int) * ((size_t)d.n + 1), sizeof(int) * (size_t)d.nnz, sizeof(double) * (size_t)d.nnz};
@@ -790,7 +813,8 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
         for (void *p : tmp)
             if (p) cudaFree(p);
         if (st != F3R_OK) return fail(st);
-        hs[k] = bt::Sys{c->n, c->nslices, c->sptr, c->col, c->a64, c->a32, c->a16, c->dsc, (const h16 *)c->mvec};
+        hs[k] = bt::Sys{c->n, c->nslices, c->sptr, c->col, c->a64, c->a32, c->a16, c->dsc, (const h16 *)c->mvec,
+                        c->m_unit ? 1 : 0};
         for (int r = 0; r < d.nrhs; ++r) {
             b->inst_sys.push_back(k);
             b->inst_rhs.push_back(r);
@@ -805,10 +829,12 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
         const Ctx &c = *b->sys[b->inst_sys[q]];
         const size_t ld = c.ld;
         bt::Inst &I = b->h_inst[q];
+        I = bt::Inst{};
         I.sys = b->inst_sys[q];
         I.ld = (int)ld;
         I.b = nullptr;
         I.x = nullptr;
+        if (b->full[I.sys]) continue;  // solved by its single-system context
         I.V1 = (double *)balloc(b, sizeof(double) * ld * (m1 + 1));
         I.Z1 = (double *)balloc(b, sizeof(double) * ld * m1);
         I.w1 = (double *)balloc(b, sizeof(double) * ld);
@@ -833,13 +859,14 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
     b->d_out = (bt::Out *)balloc(b, sizeof(bt::Out) * ninst);
     if (!b->d_sys || !b->d_inst || !b->d_order || !b->d_queue || !b->d_out) return fail(F3R_ERR_NOMEM);
     cudaMemcpyAsync(b->d_sys, hs.data(), sizeof(bt::Sys) * nsys, cudaMemcpyHostToDevice, s);
-    // largest instances first
-    std::vector<int> order(ninst);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    // the persistent launch's instances, largest first
+    for (int q = 0; q < ninst; ++q)
+        if (!b->full[b->inst_sys[q]]) b->small.push_back(q);
+    std::stable_sort(b->small.begin(), b->small.end(), [&](int a, int c) {
         return b->sys[b->inst_sys[a]]->nnz > b->sys[b->inst_sys[c]]->nnz;
     });
-    cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * ninst, cudaMemcpyHostToDevice, s);
+    if (!b->small.empty())
+        cudaMemcpyAsync(b->d_order, b->small.data(), sizeof(int) * b->small.size(), cudaMemcpyHostToDevice, s);
     b->P = bt::BP{m1, m2, m3, prm.c, prm.max_outer, prm.cgs_passes, prm.scale_cast, prm.tol, (float)prm.omega_fixed};
     b->cluster = 8;
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(F3R_ERR_CUDA);
@@ -853,9 +880,15 @@ f3r_status f3r_batched_set_cluster(f3r_batch *b, int cluster_size) {
     return F3R_OK;
 }
 
-f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const *X, f3r_batch_result *res,
-                             void *stream) {
-    if (!b || !B || !X) return F3R_ERR_ARG;
+}  // extern "C"
+
+namespace {
+// The persistent launch over the instances of the small systems; their
+// statuses go to st[q] (and res[q] when given).
+f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, f3r_batch_result *res,
+                        std::vector<int> &st, void *stream) {
+    const int nsmall = (int)b->small.size();
+    if (nsmall == 0) return F3R_OK;
     cudaStream_t s = b->cs;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -887,12 +920,12 @@ f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const
         cudaGetLastError();
         ncl = 1;
     }
-    ncl = std::min(ncl, ninst);
+    ncl = std::min(ncl, nsmall);
     cfg.gridDim = dim3(ncl * cl, 1, 1);
     b->grid = ncl * cl;
     cudaEventRecord(e0, s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, bt::k_batch, (const bt::Sys *)b->d_sys, (const bt::Inst *)b->d_inst,
-                                       (const int *)b->d_order, ninst, b->P, b->d_queue, b->d_out);
+                                       (const int *)b->d_order, nsmall, b->P, b->d_queue, b->d_out);
     cudaEventRecord(e1, s);
     if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         cudaEventDestroy(e0);
@@ -904,9 +937,8 @@ f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const
     cudaEventElapsedTime(&ms, e0, e1);
     std::vector<bt::Out> ho(ninst);
     cudaMemcpy(ho.data(), b->d_out, sizeof(bt::Out) * ninst, cudaMemcpyDeviceToHost);
-    f3r_status worst = F3R_OK;
-    for (int q = 0; q < ninst; ++q) {
-        if (ho[q].status != F3R_OK && worst == F3R_OK) worst = (f3r_status)ho[q].status;
+    for (int q : b->small) {
+        st[q] = ho[q].status;
         if (res) {
             res[q].status = ho[q].status;
             res[q].outer_iters = ho[q].outer_iters;
@@ -923,12 +955,47 @@ f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const
     cudaStreamWaitEvent((cudaStream_t)stream, e1, 0);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    return worst;
+    return F3R_OK;
+}
+}  // namespace
+
+extern "C" {
+
+f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const *X, f3r_batch_result *res,
+                             void *stream) {
+    if (!b || !B || !X) return F3R_ERR_ARG;
+    const int ninst = (int)b->h_inst.size();
+    std::vector<int> st(ninst, F3R_OK);
+    // instances of the large systems, one after another on the whole GPU
+    for (int q = 0; q < ninst; ++q) {
+        f3r_ctx *h = b->full[b->inst_sys[q]];
+        if (!h) continue;
+        f3r_stats ss{};
+        const f3r_status r = f3r_solve(h, B[q], X[q], &ss, stream);
+        if (r != F3R_OK && r != F3R_NOT_CONVERGED && r != F3R_ERR_NONFINITE) return r;
+        st[q] = r;
+        if (res) {
+            res[q].status = r;
+            res[q].outer_iters = ss.outer_iters;
+            res[q].restarts = ss.restarts;
+            res[q].rel_res_true = ss.rel_res_true;
+            res[q].m_applies = ss.m_applies;
+            res[q].r_calls = ss.r_calls;
+            res[q].t_solve_ms = ss.t_solve_ms;
+            res[q].system = b->inst_sys[q];
+            res[q].rhs = b->inst_rhs[q];
+        }
+    }
+    const f3r_status e = launch_small(b, B, X, res, st, stream);
+    if (e != F3R_OK) return e;
+    for (int q = 0; q < ninst; ++q)
+        if (st[q] != F3R_OK) return (f3r_status)st[q];
+    return F3R_OK;
 }
 
 // Autotuner of the batched launch shape: time one outer iteration of the
-// whole batch (from x0 = 0) for every cluster size that fits, keep the
-// fastest.  X is zeroed again on return.
+// persistent launch's instances (from x0 = 0) for every cluster size that
+// fits, keep the fastest.  X is zeroed again on return.
 f3r_status f3r_batched_autotune(f3r_batch *b, const double *const *B, double *const *X, int *chosen, void *stream) {
     if (!b || !B || !X) return F3R_ERR_ARG;
     const int saved_outer = b->P.max_outer;
@@ -942,10 +1009,12 @@ f3r_status f3r_batched_autotune(f3r_batch *b, const double *const *B, double *co
     for (int ci = 0; ci < 4; ++ci) {
         b->cluster = cand[ci];
         b->P.max_outer = 1;
-        for (int q = 0; q < ninst; ++q)
-            cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
+        for (int q : b->small) cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
         cudaEventRecord(e0, b->cs);
-        f3r_status st = f3r_solve_batched(b, B, X, nullptr, stream);
+        std::vector<int> stv(ninst, F3R_OK);
+        f3r_status st = launch_small(b, B, X, nullptr, stv, stream);
+        for (int q : b->small)
+            if (st == F3R_OK && stv[q] != F3R_OK) st = (f3r_status)stv[q];
         cudaEventRecord(e1, b->cs);
         cudaEventSynchronize(e1);
         float ms = 0.0f;
@@ -971,6 +1040,8 @@ int64_t f3r_batched_device_bytes(const f3r_batch *b) {
     if (!b) return 0;
     long long t = b->bytes;
     for (Ctx *c : b->sys) t += c->bytes;
+    for (f3r_ctx *h : b->full)
+        if (h) t += f3r_device_bytes(h);
     return t;
 }
 
@@ -980,6 +1051,8 @@ void f3r_destroy_batched(f3r_batch *b) {
         for (void *p : c->allocs) pool_free(p, b->cs);
         delete c;
     }
+    for (f3r_ctx *h : b->full)
+        if (h) f3r_destroy(h);
     for (void *p : b->allocs) cudaFree(p);
     if (b->cs) {
         cudaStreamSynchronize(b->cs);

@@ -216,6 +216,10 @@ struct StagePlan {
 StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize);
 // stream-ordered device memory from the per-device pool (mem.cu)
 void *pool_alloc(int dev, size_t bytes, cudaStream_t s);
+// Raise the dynamic shared memory limit of a kernel to at least `bytes`,
+// never lowering it: contexts of different sizes in one process share the
+// kernel, and a plan made by one must still launch after another's (mem.cu)
+bool ensure_dyn_smem(const void *kern, int bytes);
 void pool_free(void *p, cudaStream_t s);
 int maxd_bucket(int m);
 

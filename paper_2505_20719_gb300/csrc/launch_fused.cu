@@ -36,10 +36,7 @@ template <class K> FusedPlan fused_plan(const Ctx &c, K kern, int tsize) {
         const int chunk = ceil_div(per, kFusedChunkAlign) * kFusedChunkAlign;
         const int smem = chunk * tsize;
         if (smem > 200 * 1024) continue;
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
+        if (!ensure_dyn_smem((const void *)kern, smem)) continue;
         int nb = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kFusedThreads, smem) != cudaSuccess) {
             cudaGetLastError();
@@ -198,7 +195,7 @@ template <int S, int MAXD> bool step_go(Ctx &c, int d, int j, bool last, cudaStr
             const int per = ceil_div(ntiles, G);
             const long long smem = kBarBytes + (long long)S * sp.stage_bytes + (long long)per * kTileRows * 4;
             if (smem > 220 * 1024) continue;
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            if (!ensure_dyn_smem((const void *)kern, (int)smem)) {
                 cudaGetLastError();
                 continue;
             }

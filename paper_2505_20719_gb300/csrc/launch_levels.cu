@@ -134,7 +134,7 @@ void launch_normalize(Ctx &c, int d, bool from_w, int dst, cudaStream_t s) {
 // ------------------------------------------------------------ SpMV + dots
 // grid of a staged kernel: the blocks that fit on the SMs at once (<= 4 per SM)
 template <class K> static int staged_grid(Ctx &c, K kern, int smem, int work_blocks) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    ensure_dyn_smem((const void *)kern, smem);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStagedThreads, smem);
     nb = std::max(1, std::min(nb, 8));

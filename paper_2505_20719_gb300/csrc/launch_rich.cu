@@ -13,7 +13,7 @@ template <class TC> static RichDev<TC> richdev(Ctx &c) {
 }
 
 template <class K> static int rich_grid(Ctx &c, K kern, int smem) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    ensure_dyn_smem((const void *)kern, smem);
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kStagedThreads, smem);
     nb = std::max(1, std::min(nb, 8));

@@ -52,6 +52,23 @@ void pool_free(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
 }
 
+namespace {
+std::mutex g_smem_mu;
+std::map<const void *, int> g_smem;  // limit set per kernel (this device)
+}  // namespace
+
+bool ensure_dyn_smem(const void *kern, int bytes) {
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    int &cur = g_smem[kern];
+    if (bytes <= cur) return true;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cur = bytes;
+    return true;
+}
+
 }  // namespace f3r
 
 extern "C" f3r_status f3r_trim_memory(void) {

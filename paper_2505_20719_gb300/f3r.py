@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("row_scale", C.c_int), ("scale_cast", C.c_int), ("cgs_passes", C.c_int), ("tol", C.c_double),
         ("max_outer", C.c_int), ("use_graphs", C.c_int), ("keep_omega", C.c_int), ("fuse_cgs", C.c_int),
         ("inner_rtol", C.c_float), ("ainv_alpha", C.c_float),
-        ("fuse_step", C.c_int), ("reserved", C.c_int * 3),
+        ("fuse_step", C.c_int), ("batch_split", C.c_int), ("reserved", C.c_int * 2),
     ]
 
 

@@ -63,3 +63,36 @@ def test_batched_instance_matches_oracle(batch):
     assert code == f3r.OK and ref.status == O.OK
     assert abs(res[0].outer_iters - ref.outer_iters) <= max(1, ref.outer_iters // 10)
     assert np.linalg.norm(x.cpu().numpy() - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+
+
+def test_batched_split_large_systems_to_single_path(batch):
+    """Systems of at least batch_split rows are solved one after another by the
+    single-system path: their results are bit for bit those of a separate
+    f3r_solve; the rest still go through the persistent launch and converge."""
+    split = 5000
+    assert any(p.n >= split for p, _ in batch) and any(p.n < split for p, _ in batch)
+    systems = [(dev(p.rowptr), dev(p.colidx), dev(p.val), B.shape[0]) for p, B in batch]
+    bs = f3r.BatchedSolver(systems, f3r.default_params(batch_split=split))
+    Bs, Xs, meta = [], [], []
+    for k, (p, B) in enumerate(batch):
+        for r in range(B.shape[0]):
+            Bs.append(dev(B[r]))
+            Xs.append(torch.zeros(p.n, dtype=torch.float64, device="cuda"))
+            meta.append((k, r))
+    bs.autotune(Bs, Xs)
+    code, res = bs.solve(Bs, Xs)
+    torch.cuda.synchronize()
+    assert code == f3r.OK
+    for q, (k, r) in enumerate(meta):
+        p, B = batch[k]
+        x = Xs[q].cpu().numpy()
+        rel = np.linalg.norm(B[r] - p.to_scipy() @ x) / np.linalg.norm(B[r])
+        assert res[q].status == f3r.OK and res[q].system == k and res[q].rhs == r and rel < 1e-9
+        if p.n >= split:
+            s = f3r.Solver(dev(p.rowptr), dev(p.colidx), dev(p.val), f3r.default_params(batch_split=split))
+            xs = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+            rs = s.solve(dev(B[r]), xs)
+            assert rs.outer_iters == res[q].outer_iters
+            assert torch.equal(xs, Xs[q])
+            s.close()
+    bs.close()

@@ -441,3 +441,21 @@ def test_pooled_context_memory_reused_and_trimmed():
     x = np.zeros(prob.n)
     assert s.solve(np.ascontiguousarray(prob.b), x).outer_iters == out[0][1]
     assert np.array_equal(x, out[0][0])
+
+
+def test_contexts_with_different_stage_sizes_interleave():
+    """Staged kernels size their shared memory from the matrix's slice width:
+    a context set up and solved after another one with wider slices must not
+    leave the first one unable to launch (replaying its graphs)."""
+    p3 = G.diffusion3d_7pt(dims=(22, 20, 18), seed=111)
+    p2 = G.poisson2d_5pt(60)
+    s3 = solver(p3, f3r.default_params())
+    x3 = np.zeros(p3.n)
+    r3 = s3.solve(np.ascontiguousarray(p3.b), x3)
+    s2 = solver(p2, f3r.default_params(diag_scale=0))
+    x2 = np.zeros(p2.n)
+    assert s2.solve(np.ascontiguousarray(p2.b), x2).status == f3r.OK
+    y3 = np.zeros(p3.n)
+    r3b = s3.solve(np.ascontiguousarray(p3.b), y3)
+    assert r3.status == f3r.OK and r3b.status == f3r.OK
+    assert r3b.outer_iters == r3.outer_iters and np.array_equal(x3, y3)
