@@ -73,22 +73,29 @@ __device__ __forceinline__ void bulk_g2s_hint(uint32_t dst, const void *src, uin
 }
 
 
+// A waiting thread may be suspended for up to kSuspendNs inside one
+// try_wait (it resumes as soon as the phase completes), so a warp that waits
+// for a stage does not spin through issue slots the working warps need.
+constexpr unsigned kSuspendNs = 20000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "n"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
 
 // Bounded, warp-uniform wait for phase `parity` of a barrier: every lane
 // polls (so each lane acquires the completed phase), the warp leaves together
-// once all lanes saw it, and gives up after kWaitCycles of lane 0's clock.
+// once all lanes saw it, and gives up after kWaitCycles of lane 0's clock
+// (read only once the first poll found the phase incomplete).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
     const long long t0 = __shfl_sync(0xffffffffu, (long long)clock64(), 0);
     for (;;) {
         const bool ok = mbar_try_wait(bar, parity);
