@@ -239,16 +239,17 @@ __device__ __forceinline__ TC sell_row(const Sell &S, const TA *__restrict__ val
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
-// Programmatic dependent launch: a kernel first lets the next kernel in the
-// stream start launching (its blocks fill SMs as this grid drains), then waits
-// until every prerequisite grid has completed and its writes are visible.
-// Both are no-ops for a launch without the programmatic attribute.
-__device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
+// Programmatic dependent launch.  pdl_wait: wait until every prerequisite
+// grid has completed and its writes are visible (a kernel launched with the
+// programmatic attribute calls it before touching anything an earlier kernel
+// writes).  pdl_trigger: let the next kernel in the stream start launching
+// (its blocks run their prologue as this grid drains); without it that
+// happens when this grid exits.  Both are no-ops without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() { pdl_wait(); }
 
-// programmatic dependent launch, on when F3R_PDL=1 is set in the environment
+// programmatic dependent launch, on unless F3R_PDL=0 is set in the environment
 bool pdl_enabled();
 
 // launch with the programmatic-stream-serialization attribute

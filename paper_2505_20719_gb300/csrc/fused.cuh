@@ -257,6 +257,8 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8) ? 2 : 1)
         if (threadIdx.x < 2) part2[(size_t)blockIdx.x * 2 + threadIdx.x] = tot[threadIdx.x];
         ok = coop_sync(fs.bar, (passes == 2 ? 2u : 1u) * (unsigned)G, fs.err);
     }
+    // the next kernel (a programmatic launch) may start its prologue now
+    pdl_trigger();
 
     // ---- Givens step (block 0) and phase C: normalise into V[j+1] and the child
     if (ok) {

@@ -363,8 +363,8 @@ StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize) {
 
 bool pdl_enabled() {
     static const bool on = [] {
-        const char *e = getenv("F3R_PDL");
-        return e && e[0] == '1';
+        const char *e = getenv("F3R_PDL");  // 0: plain stream order for every launch
+        return !(e && e[0] == '0');
     }();
     return on;
 }

@@ -149,10 +149,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // owning slice s.  Every wait is bounded; a consumer that gives up records
 // the error and stops, the producer stops refilling after a failed wait and
 // finally waits (bounded) for the copies it issued.
-template <class TA, int S, bool EVICT_FIRST = false, class Body>
-__device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict__ val, int tile_begin,
-                                             int tile_end, char *ring, int stage_bytes, uint64_t *full,
-                                             uint64_t *empty, Extra ex, int *err, Body body) {
+// gate(): evaluated by every thread once the producer has issued the copies
+// of the first S tiles (the matrix and the extras, which no kernel still
+// running writes): it waits for the prerequisite grids and returns false
+// when the kernel has nothing to do; the producer then waits for the copies
+// it issued and the call returns false.
+template <class TA, int S, bool EVICT_FIRST = false, class Body, class Gate>
+__device__ __forceinline__ bool staged_tiles_gated(const Sell &A, const TA *__restrict__ val, int tile_begin,
+                                                   int tile_end, char *ring, int stage_bytes, uint64_t *full,
+                                                   uint64_t *empty, Extra ex, int *err, Body body, Gate gate) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool producer = (warp == kWarps);
     // run by the whole producer warp: lanes 0..8 write the tile's slice
@@ -201,9 +206,18 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
     __syncthreads();
     bool ok = true;
     if (producer) {
-        fence_proxy_async_all();  // the basis rows the previous kernel wrote, before the first bulk copy
+        fence_proxy_async_all();  // the basis rows an earlier kernel wrote, before the first bulk copy
         int k = 0;
-        for (int t = tile_begin; t < tile_end; ++t, ++k) {
+        const int pre = min(S, max(0, tile_end - tile_begin));
+        for (; k < pre; ++k) {
+            issue(tile_begin + k, k);
+            __syncwarp();
+        }
+        if (!gate()) {
+            for (int kk = 0; kk < pre; ++kk) mbar_wait(smem_u32(full + kk), 0u);
+            return false;
+        }
+        for (int t = tile_begin + k; t < tile_end; ++t, ++k) {
             const int st = k % S;
             if (k >= S && !mbar_wait(smem_u32(empty + st), (uint32_t)(((k / S) - 1) & 1))) {
                 ok = false;
@@ -218,6 +232,7 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
             mbar_wait(smem_u32(full + kk % S), (uint32_t)((kk / S) & 1));
         if (!ok && lane == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
     } else {
+        if (!gate()) return false;
         int k = 0;
         for (int t = tile_begin; t < tile_end; ++t, ++k) {
             const int st = k % S;
@@ -248,6 +263,15 @@ __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict
         }
     }
     return ok;
+}
+
+// staged_tiles_gated without a gate (the caller waited already)
+template <class TA, int S, bool EVICT_FIRST = false, class Body>
+__device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict__ val, int tile_begin,
+                                             int tile_end, char *ring, int stage_bytes, uint64_t *full,
+                                             uint64_t *empty, Extra ex, int *err, Body body) {
+    return staged_tiles_gated<TA, S, EVICT_FIRST>(A, val, tile_begin, tile_end, ring, stage_bytes, full, empty, ex,
+                                                  err, body, [] { return true; });
 }
 
 // stage size in bytes for tiles of slices up to wmax wide

@@ -70,8 +70,8 @@ template <class TA, class T, int S, int MAXD>
 __global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const TA *__restrict__ val,
                                                          const float *__restrict__ rs, LevelDev<T> L, int j,
                                                          GridRed<T> gr, StageCfg cfg, T *hpart) {
-    pdl_enter();
-    if (stopped(L.flags, L.depth)) return;
+    // programmatic launch: the matrix and basis tiles of the first stages are
+    // requested before the wait for the Richardson call that writes z
     extern __shared__ __align__(128) char dsm[];
     const int lane = threadIdx.x & 31;
     const T *__restrict__ x = L.Z + (size_t)j * L.ld;
@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const T
     ex.ld = L.ld;
     ex.esize = sizeof(T);
     const int2 tr = tile_range(A);
-    staged_tiles<TA, S, true>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), ex, cfg.err,
+    bool go = false;  // the gate passed (the same in every thread)
+    staged_tiles_gated<TA, S, true>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), ex, cfg.err,
                         [&](int s, const StageView<TA> &v) {
                              T y = staged_row<T>(v, lane, [&](int c) { return __ldg(x + c); });
                              const int i = s * kSlice + lane;
@@ -95,7 +96,14 @@ __global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const T
                                  for (int l = 0; l < MAXD; ++l)
                                      if (l <= j) acc[l] = fma_rn(v.template ext<T>(l)[lane], y, acc[l]);
                              }
-                         });
+                         },
+                        [&] {
+                            pdl_wait();
+                            go = !stopped(L.flags, L.depth);
+                            return go;
+                        });
+    if (!go) return;  // a stopped level, in every block alike
+    pdl_trigger();
     if (hpart) {
         block_partials<T, MAXD>(acc, j + 1, hpart);
         return;
@@ -113,14 +121,15 @@ __global__ void __launch_bounds__(kStagedThreads) k_rich2_st(Sell A, const TA *_
                                                      const VS *__restrict__ v, const VS *__restrict__ mv, TP *out,
                                                      const TP *par_misc, RichDev<TC> R, const int *flags,
                                                      int check_depth, int n, StageCfg cfg) {
-    pdl_enter();
-    if (stopped(flags, check_depth)) return;
+    // programmatic launch: the first stages' matrix tiles are requested
+    // before the wait for the kernel that writes v, the weights and sigma
     extern __shared__ __align__(128) char dsm[];
     const int lane = threadIdx.x & 31;
-    const TC w1 = R.omega[0], w2 = R.omega[1];
-    const TP inv_sigma = par_misc[MS_INV_SIGMA];
+    TC w1 = (TC)0, w2 = (TC)0;
+    TP inv_sigma = (TP)1;
     const int2 tr = tile_range(A);
-    staged_tiles<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), Extra(), cfg.err,
+    bool go = false;  // the gate passed (the same in every thread)
+    staged_tiles_gated<TA, S>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), Extra(), cfg.err,
                         [&](int s, const StageView<TA> &st) {
                              TC acc = staged_row<TC>(st, lane, [&](int c) {
                                  const TC vc = to_c<TC>(__ldg(v + c));
@@ -135,7 +144,18 @@ __global__ void __launch_bounds__(kStagedThreads) k_rich2_st(Sell A, const TA *_
                                  const TC z2 = rnd<VS>(fma_rn(w2, UNIT ? ri : mul_rn(to_c<TC>(mv[i]), ri), z1));
                                  out[i] = mul_rn((TP)z2, inv_sigma);
                              }
-                         });
+                         },
+                        [&] {
+                            pdl_wait();
+                            if (stopped(flags, check_depth)) return false;
+                            w1 = R.omega[0];
+                            w2 = R.omega[1];
+                            inv_sigma = par_misc[MS_INV_SIGMA];
+                            go = true;
+                            return true;
+                        });
+    if (!go) return;
+    pdl_trigger();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         atomicAdd(R.counters + 0, 2ull);
         atomicAdd(R.counters + 1, 1ull);

@@ -459,3 +459,31 @@ def test_contexts_with_different_stage_sizes_interleave():
     r3b = s3.solve(np.ascontiguousarray(p3.b), y3)
     assert r3.status == f3r.OK and r3b.status == f3r.OK
     assert r3b.outer_iters == r3.outer_iters and np.array_equal(x3, y3)
+
+
+def test_programmatic_launch_changes_no_result(tmp_path):
+    """Programmatic dependent launch (the default) only lets a kernel's
+    prologue overlap the previous kernel: a solve in a process with it turned
+    off (F3R_PDL=0) gives the same bits."""
+    import os
+    import subprocess
+    import sys
+
+    prob = G.diffusion3d_7pt(dims=(30, 28, 26), seed=112)
+    s = solver(prob, f3r.default_params())
+    x = np.zeros(prob.n)
+    r = s.solve(np.ascontiguousarray(prob.b), x)
+    out = tmp_path / "x.npy"
+    code = (
+        "import numpy as np, sys; sys.path.insert(0, %r)\n"
+        "from problems import generators as G\n"
+        "from paper_2505_20719_gb300 import f3r\n"
+        "p = G.diffusion3d_7pt(dims=(30, 28, 26), seed=112)\n"
+        "s = f3r.Solver.from_problem(p, f3r.default_params())\n"
+        "x = np.zeros(p.n); r = s.solve(np.ascontiguousarray(p.b), x)\n"
+        "np.save(%r, np.append(x, r.outer_iters))\n"
+    ) % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))), str(out))
+    env = dict(os.environ, F3R_PDL="0")
+    subprocess.run([sys.executable, "-c", code], env=env, check=True, timeout=300)
+    y = np.load(out)
+    assert int(y[-1]) == r.outer_iters and np.array_equal(y[:-1], x)
