@@ -339,7 +339,7 @@ int64_t f3r_device_bytes(const f3r_ctx *ctx);
 void f3r_destroy(f3r_ctx *ctx);
 
 /* Returns the device memory that the library's pools keep but no context uses
- * to the driver.  Contexts' own buffers are not touched. */
+ * to the CUDA driver.  Contexts' own buffers are not touched. */
 f3r_status f3r_trim_memory(void);
 const char *f3r_status_str(f3r_status s);
 

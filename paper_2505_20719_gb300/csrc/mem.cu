@@ -3,7 +3,7 @@
 // threshold at the maximum).  A process that sets up and destroys contexts
 // repeatedly then reuses device memory without a cudaMalloc / cudaFree (and
 // the device-wide synchronisation of cudaFree) per buffer.  f3r_trim_memory
-// returns the unused blocks to the driver.
+// returns the unused blocks to the CUDA driver.
 #include <cstdint>
 #include <map>
 #include <mutex>
