@@ -41,8 +41,41 @@ __device__ __forceinline__ int2 tile_range(const Sell &A) {
 // round of gather latency, not one per entry (the accumulation order is
 // unchanged).
 constexpr int kRowGroup = 8;
+
+// a slice exactly W entries wide: W gathers issued, then W fused multiply-adds
+// (no slot of the group is spent on entries past the width)
+template <class TC, int W, class TA, class GX>
+__device__ __forceinline__ TC staged_row_w(const StageView<TA> &v, int lane, GX gx) {
+    int c[W];
+    TC a[W], xv[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        c[q] = v.col[q * kSlice + lane];
+        a[q] = to_c<TC>(v.val[q * kSlice + lane]);
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) xv[q] = (c[q] >= 0) ? gx(c[q]) : (TC)0;
+    TC acc = (TC)0;
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+        if (c[q] >= 0) acc = fma_rn(a[q], xv[q], acc);
+    return acc;
+}
+
 template <class TC, class TA, class GX>
 __device__ __forceinline__ TC staged_row(const StageView<TA> &v, int lane, GX gx) {
+    switch (v.w) {  // slice widths up to one group: exact-width code
+        case 0: return (TC)0;
+        case 1: return staged_row_w<TC, 1>(v, lane, gx);
+        case 2: return staged_row_w<TC, 2>(v, lane, gx);
+        case 3: return staged_row_w<TC, 3>(v, lane, gx);
+        case 4: return staged_row_w<TC, 4>(v, lane, gx);
+        case 5: return staged_row_w<TC, 5>(v, lane, gx);
+        case 6: return staged_row_w<TC, 6>(v, lane, gx);
+        case 7: return staged_row_w<TC, 7>(v, lane, gx);
+        case 8: return staged_row_w<TC, 8>(v, lane, gx);
+        default: break;
+    }
     TC acc = (TC)0;
     for (int k0 = 0; k0 < v.w; k0 += kRowGroup) {
         int c[kRowGroup];
