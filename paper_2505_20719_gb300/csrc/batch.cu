@@ -198,11 +198,43 @@ __device__ void ls_column(LS &L, int m, int j, const float *hcol, float hn, bool
 __device__ __forceinline__ float pow2_scale_f(float a) { return pow2_scale_for(a); }
 
 // ----------------------------------------------------------- team kernels
+// row sum of a slice exactly W entries wide: W gathers, then W fused
+// multiply-adds in CSR order (no slot past the width)
+template <class TC, int W, class TA, class GX>
+__device__ __forceinline__ TC row_sum_w(const Sys &S, const TA *val, int beg, GX gx) {
+    int c[W];
+    TC a[W], xv[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        c[q] = __ldg(S.col + beg + (q << 5));
+        a[q] = to_c<TC>(__ldg(val + beg + (q << 5)));
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) xv[q] = (c[q] >= 0) ? gx(c[q]) : (TC)0;
+    TC acc = (TC)0;
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+        if (c[q] >= 0) acc = fma_rn(a[q], xv[q], acc);
+    return acc;
+}
+
 // row sum of slice row i over A (CSR order, fused multiply-add), x from gx
 template <class TC, class TA, class GX>
 __device__ __forceinline__ TC row_sum(const Sys &S, const TA *val, int s, int lane, GX gx) {
     const int beg = __ldg(S.sptr + s) + lane;
     const int w = (__ldg(S.sptr + s + 1) - __ldg(S.sptr + s)) >> 5;
+    switch (w) {  // slices up to 8 wide: exact-width code
+        case 0: return (TC)0;
+        case 1: return row_sum_w<TC, 1>(S, val, beg, gx);
+        case 2: return row_sum_w<TC, 2>(S, val, beg, gx);
+        case 3: return row_sum_w<TC, 3>(S, val, beg, gx);
+        case 4: return row_sum_w<TC, 4>(S, val, beg, gx);
+        case 5: return row_sum_w<TC, 5>(S, val, beg, gx);
+        case 6: return row_sum_w<TC, 6>(S, val, beg, gx);
+        case 7: return row_sum_w<TC, 7>(S, val, beg, gx);
+        case 8: return row_sum_w<TC, 8>(S, val, beg, gx);
+        default: break;
+    }
     TC acc = (TC)0;
     constexpr int U = 4;  // loads of a group of entries issued before its multiply-adds
     for (int k0 = 0; k0 < w; k0 += U) {

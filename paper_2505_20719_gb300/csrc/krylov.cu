@@ -27,6 +27,44 @@ namespace f3r {
 
 namespace {
 
+// fp64 row sum of a slice exactly W entries wide: W gathers, then W fused
+// multiply-adds in CSR order (no slot past the width)
+template <int W, class GX>
+__device__ __forceinline__ double kry_row_w(const Sell &S, const double *__restrict__ a, int beg, GX gx) {
+    int c[W];
+    double v[W], xv[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        c[q] = __ldg(S.col + beg + (q << 5));
+        v[q] = __ldg(a + beg + (q << 5));
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) xv[q] = (c[q] >= 0) ? gx(c[q]) : 0.0;
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < W; ++q)
+        if (c[q] >= 0) acc = fma_rn(v[q], xv[q], acc);
+    return acc;
+}
+
+// the same row sum as sell_row, with exact-width code for slices up to 8 wide
+template <class GX>
+__device__ __forceinline__ double kry_row(const Sell &S, const double *__restrict__ a, int s, int lane, GX gx) {
+    const int beg = __ldg(S.sptr + s) + lane;
+    switch ((__ldg(S.sptr + s + 1) - __ldg(S.sptr + s)) >> 5) {
+        case 0: return 0.0;
+        case 1: return kry_row_w<1>(S, a, beg, gx);
+        case 2: return kry_row_w<2>(S, a, beg, gx);
+        case 3: return kry_row_w<3>(S, a, beg, gx);
+        case 4: return kry_row_w<4>(S, a, beg, gx);
+        case 5: return kry_row_w<5>(S, a, beg, gx);
+        case 6: return kry_row_w<6>(S, a, beg, gx);
+        case 7: return kry_row_w<7>(S, a, beg, gx);
+        case 8: return kry_row_w<8>(S, a, beg, gx);
+        default: return sell_row<double>(S, a, s, lane, gx);
+    }
+}
+
 constexpr int kKrylovBatch = 16;  // iterations per graph replay
 constexpr int kHistCap = 1 << 20;
 
@@ -68,7 +106,7 @@ __global__ void __launch_bounds__(kBlock) k_kry_init(Sell S, const double *__res
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int s = wid; s < S.nslices; s += nw) {
-        const double ax = sell_row<double>(S, a, s, lane, [&](int c) { return __ldg(K.x + c); });
+        const double ax = kry_row(S, a, s, lane, [&](int c) { return __ldg(K.x + c); });
         const int i = s * kSlice + lane;
         if (i < K.n) {
             const double ri = sub_rn(b[i], ax);
@@ -119,7 +157,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_q(Sell S, const double *__restric
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     auto pdir = [&](int c) { return fma_rn(beta, __ldg(pp + c), __ldg(K.z + c)); };
     for (int s = wid; s < S.nslices; s += nw) {
-        const double qi = sell_row<double>(S, a, s, lane, pdir);
+        const double qi = kry_row(S, a, s, lane, pdir);
         const int i = s * kSlice + lane;
         if (i < K.n) {
             const double pi = pdir(i);
@@ -188,7 +226,7 @@ __global__ void __launch_bounds__(kBlock) k_bs_spmv(Sell S, const double *__rest
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int s = wid; s < S.nslices; s += nw) {
-        const double yi = sell_row<double>(S, a, s, lane, [&](int c) { return __ldg(src + c); });
+        const double yi = kry_row(S, a, s, lane, [&](int c) { return __ldg(src + c); });
         const int i = s * kSlice + lane;
         if (i < K.n) {
             y[i] = yi;
@@ -261,7 +299,7 @@ __global__ void __launch_bounds__(kBlock) k_kry_true(Sell S, const double *__res
     const int lane = threadIdx.x & 31;
     const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int s = wid; s < S.nslices; s += nw) {
-        const double ax = sell_row<double>(S, a, s, lane, [&](int c) { return __ldg(K.x + c); });
+        const double ax = kry_row(S, a, s, lane, [&](int c) { return __ldg(K.x + c); });
         const int i = s * kSlice + lane;
         if (i < K.n) {
             const double ri = sub_rn(b[i], ax);
