@@ -61,3 +61,39 @@ def test_cuda_sources_target_sm103a_only():
     for f in os.listdir(src):
         text = open(os.path.join(src, f)).read()
         assert "oracle" not in text.lower() or f.endswith(".md"), f
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's size
+    and field offsets (compiled against include/f3r.h with gcc)."""
+    import shutil
+    import subprocess
+
+    from paper_2505_20719_gb300 import f3r
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"f3r_params": f3r.Params, "f3r_stats": f3r.Stats, "f3r_system_desc": f3r.SystemDesc,
+               "f3r_batch_result": f3r.BatchResult}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "f3r.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line:
+            continue
+        cname, key, value = line.split()
+        py = structs[cname]
+        want = ctypes.sizeof(py) if key == "size" else getattr(py, key).offset
+        assert int(value) == want, (cname, key, value, want)
+        seen += 1
+    assert seen == sum(1 + len(py._fields_) for py in structs.values())
