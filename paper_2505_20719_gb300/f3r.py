@@ -373,8 +373,10 @@ class Solver:
 
 
 class BatchedSolver:
-    """Many systems (each with nrhs right-hand sides) solved in one persistent
-    launch: f3r_setup_batched / f3r_solve_batched."""
+    """Many systems (each with nrhs right-hand sides): f3r_setup_batched /
+    f3r_solve_batched.  Instances of systems below params.batch_split rows are
+    solved in one persistent launch (one thread-block cluster each), larger
+    systems one after another by the single-system path."""
 
     def __init__(self, systems, params: Params = None, stream=None):
         """systems: list of (rowptr, colidx, val, nrhs) with host (numpy) or
