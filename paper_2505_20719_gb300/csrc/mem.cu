@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <utility>
 
 #include "ctx.h"
 
@@ -54,12 +55,17 @@ void pool_free(void *p, cudaStream_t s) {
 
 namespace {
 std::mutex g_smem_mu;
-std::map<const void *, int> g_smem;  // limit set per kernel (this device)
+std::map<std::pair<int, const void *>, int> g_smem;  // limit set per (device, kernel)
 }  // namespace
 
 bool ensure_dyn_smem(const void *kern, int bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
     std::lock_guard<std::mutex> lk(g_smem_mu);
-    int &cur = g_smem[kern];
+    int &cur = g_smem[std::make_pair(dev, kern)];
     if (bytes <= cur) return true;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
         cudaGetLastError();
