@@ -106,3 +106,22 @@ def test_nonfinite_pass_through(orc, prec):
     y = O.round_to(prec, x)
     assert y[0] == np.inf and y[1] == -np.inf and np.isnan(y[2])
     assert y[3] == 0 and not np.signbit(y[3]) and np.signbit(y[4])
+
+
+def test_every_float32_binade_and_sign_at_stride_256(orc):
+    """fp32 -> fp16 and fp32 -> bf16 over the fp32 bit patterns at a stride of
+    256 (every sign and exponent, every 256th significand, a seeded low byte):
+    the oracle matches numpy's float16 cast and the bit-level bfloat16
+    round-to-nearest-even formula on all 16.7 M finite inputs."""
+    low = rng.integers(7, 1, 1, 0, 255)[0]
+    bits = (np.arange(1 << 24, dtype=np.uint64) << np.uint64(8)) | np.uint64(low)
+    x32 = bits.astype(np.uint32).view(np.float32)
+    x32 = x32[np.isfinite(x32)]
+    x64 = x32.astype(np.float64)
+    got16 = O.round_to(O.F16, x64)
+    with np.errstate(over="ignore"):
+        want16 = x32.astype(np.float16).astype(np.float64)
+    same = (got16 == want16) | (np.isnan(got16) & np.isnan(want16))
+    assert np.all(same) and np.array_equal(np.signbit(got16), np.signbit(want16))
+    gotbf = O.round_to(O.BF16, x64)
+    assert np.array_equal(gotbf, _bf16_bits_rne(x32))
