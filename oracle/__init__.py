@@ -69,6 +69,9 @@ def lib():
         L.orc_solve.restype = C.c_int
         L.orc_outer_arnoldi.argtypes = [C.c_void_p, C.POINTER(Params), dp, C.c_int, dp, dp, dp]
         L.orc_outer_arnoldi.restype = C.c_int
+        L.orc_inner_arnoldi.argtypes = [C.c_void_p, C.POINTER(Params), C.POINTER(RichState), C.c_int, dp, dp,
+                                         dp, dp, dp, dp]
+        L.orc_inner_arnoldi.restype = C.c_int
         L.orc_num_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -231,6 +234,25 @@ class Problem:
         H = np.zeros((steps, steps + 1))  # column-major (steps+1) x steps
         lib().orc_outer_arnoldi(self.h, C.byref(prm), _dp(b), steps, _dp(V), _dp(Z), _dp(H))
         return V, Z, H.T.copy()
+
+    def inner_arnoldi(self, prm: Params, state: RichState, level: int, v):
+        """One call of inner FGMRES level `level` with its basis recorded.
+
+        Returns (z, V, Z, H, g, k): the level's output z, the basis V ((m+1) x n),
+        the preconditioned vectors Z (m x n), the Hessenberg matrix H ((m+1) x m,
+        before rotation), the rotated right-hand side g (m+1) and the number of
+        columns k the level kept.
+        """
+        m = prm.m[level]
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        z = np.empty(self.n)
+        V = np.zeros((m + 1, self.n))
+        Z = np.zeros((m, self.n))
+        H = np.zeros((m, m + 1))  # column-major (m+1) x m
+        g = np.zeros(m + 1)
+        k = lib().orc_inner_arnoldi(self.h, C.byref(prm), C.byref(state), level, _dp(v), _dp(z), _dp(V),
+                                    _dp(Z), _dp(H), _dp(g))
+        return z, V, Z, H.T.copy(), g, k
 
 
 def rich_state(c_ntr: int = 1, omega=None) -> RichState:

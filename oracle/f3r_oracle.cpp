@@ -310,11 +310,23 @@ void combine(const std::vector<std::vector<T>> &Z, const std::vector<T> &y, int 
 }
 
 /* ------------------------------------------------------------------ the nest */
+/* What one call of an inner FGMRES level leaves behind, for the Arnoldi and
+ * Givens pins: basis V (m+1 vectors), preconditioned vectors Z (m), the
+ * Hessenberg matrix before rotation ((m+1) x m, column-major), the rotated
+ * right-hand side g (m+1) and the number of columns kept. */
+struct InnerRecord {
+    int level = -1;
+    bool done = false;
+    double *V = nullptr, *Z = nullptr, *H = nullptr, *g = nullptr;
+    int kdim = 0;
+};
+
 struct Nest {
     const Problem &P;
     orc_params prm;
     orc_rich_state *st;
     int64_t m_applies = 0, r_calls = 0, r_update_calls = 0;
+    InnerRecord *rec = nullptr;
 
     Nest(const Problem &P_, const orc_params &prm_, orc_rich_state *st_) : P(P_), prm(prm_), st(st_) {}
 
@@ -487,7 +499,7 @@ struct Nest {
         const T rtol = (T)prm.inner_rtol;
         int ran = 0;
         std::vector<std::vector<T>> V(m + 1, std::vector<T>(n)), Z(m, std::vector<T>(n));
-        std::vector<T> w(n), hcol(m + 1);
+        std::vector<T> w(n), hcol(m + 1), Hraw((size_t)(m + 1) * m, T(0));
         Givens<T> G(m);
         T inv = (T)1 / beta;
         for (int i = 0; i < n; ++i) V[0][i] = v[i] * inv;
@@ -499,6 +511,8 @@ struct Nest {
             spmv_t<T>(P, prm.a_prec[d], Z[j].data(), w.data());
             cgs<T>(V, j, w, prm.cgs_passes, hcol);
             T hn = std::sqrt(dot_t(w.data(), w.data(), n));
+            for (int i = 0; i <= j; ++i) Hraw[i + (size_t)(m + 1) * j] = hcol[i];
+            Hraw[j + 1 + (size_t)(m + 1) * j] = hn;
             if (!std::isfinite(hn) || !all_finite(hcol.data(), j + 1)) break;  // drop column j
             if (!G.add_column(j, hcol, hn)) break;
             kdim = j + 1;
@@ -510,6 +524,22 @@ struct Nest {
         st->c_ntr += (int64_t)(m - ran) * calls_below(d);
         std::vector<T> y = G.solve(kdim);
         combine(Z, y, kdim, z, n);
+        if (rec && rec->level == d && !rec->done) record_inner(V, Z, Hraw, G, kdim, m);
+    }
+
+    /* copy one inner call's basis, Hessenberg matrix and rotated g out */
+    template <class T>
+    void record_inner(const std::vector<std::vector<T>> &V, const std::vector<std::vector<T>> &Z,
+                      const std::vector<T> &Hraw, const Givens<T> &G, int kdim, int m) {
+        const int n = P.n;
+        rec->done = true;
+        rec->kdim = kdim;
+        for (int k = 0; k <= m; ++k)
+            for (int i = 0; i < n; ++i) rec->V[(size_t)k * n + i] = (double)V[k][i];
+        for (int k = 0; k < m; ++k)
+            for (int i = 0; i < n; ++i) rec->Z[(size_t)k * n + i] = (double)Z[k][i];
+        for (int k = 0; k < (m + 1) * m; ++k) rec->H[k] = (double)Hraw[k];
+        for (int k = 0; k <= m; ++k) rec->g[k] = (double)G.g[k];
     }
 
     /* The outermost fp64 FGMRES(m1) with restarts (Sec. 4.2, Sec. 5). */
@@ -756,6 +786,30 @@ int orc_outer_arnoldi(void *p, const orc_params *prm, const double *b, int steps
     std::vector<double> x(P.n, 0.0);
     Nest N(P, q, &st);
     return N.solve(b, x.data(), nullptr, V, Z, H, steps);
+}
+
+int orc_inner_arnoldi(void *p, const orc_params *prm, orc_rich_state *st, int level, const double *v,
+                      double *z, double *V, double *Z, double *H, double *g) {
+    const Problem &P = *(const Problem *)p;
+    if (level < 1 || level >= prm->nlevels) return -1;
+    Nest N(P, *prm, st);
+    InnerRecord R;
+    R.level = level;
+    R.V = V;
+    R.Z = Z;
+    R.H = H;
+    R.g = g;
+    N.rec = &R;
+    const int n = P.n;
+    if (prm->v_prec[level] == ORC_F64) {
+        N.fgmres_inner<double>(level, v, z);
+    } else {
+        std::vector<float> vf(n), zf(n);
+        for (int i = 0; i < n; ++i) vf[i] = (float)v[i];
+        N.fgmres_inner<float>(level, vf.data(), zf.data());
+        for (int i = 0; i < n; ++i) z[i] = zf[i];
+    }
+    return R.done ? R.kdim : -1;
 }
 
 int orc_num_threads(void) {

@@ -110,6 +110,15 @@ int orc_solve(void *p, const orc_params *prm, const double *b, double *x, orc_st
 int orc_outer_arnoldi(void *p, const orc_params *prm, const double *b, int steps,
                       double *V, double *Z, double *H);
 
+/* One call of inner FGMRES level `level` (1 <= level < nlevels) on input v
+ * (the parent's vector type), recording that call's basis V (n x (m+1)),
+ * preconditioned vectors Z (n x m), Hessenberg matrix H before rotation
+ * ((m+1) x m, column-major) and rotated right-hand side g (m+1), all as
+ * float64 copies of the level's values; z receives the level's output.
+ * Returns the number of columns kept (k <= m), or -1 if nothing ran. */
+int orc_inner_arnoldi(void *p, const orc_params *prm, orc_rich_state *st, int level,
+                      const double *v, double *z, double *V, double *Z, double *H, double *g);
+
 int orc_num_threads(void);
 
 #ifdef __cplusplus

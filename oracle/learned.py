@@ -19,10 +19,14 @@ Two training losses over samples p = 1..P (means over p):
     residual  ||A M_theta(r_p) - r_p||^2 / ||r_p||^2      (A the matrix the
               preconditioned level applies, here the fp16 copy of A^)
 
-forward() / backward() are plain fp64 numpy; forward(..., bf16=True) rounds
-the weights, the stored activations and the aggregated messages to bfloat16
-(the storage formats of the CUDA kernels) to give the reference the GPU is
-compared with.  The gradient is checked against central finite differences.
+forward() / backward() are plain fp64 numpy; with bf16=True they round the
+values the network stores between its steps to bfloat16 and nothing else:
+forward -- the weights e, Ws, Wm, wo, the activations h and the aggregated
+messages g; backward -- the weights it multiplies by, the masked output
+gradients dP = bf16(dh * [h > 0]) of every layer and the messages
+u = bf16(dP Wm) it aggregates (dh itself, the weight gradients and all sums
+stay in full precision).  That is the reference the GPU is compared with.
+The fp64 gradient is checked against central finite differences.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -83,58 +87,61 @@ def forward(A_off, r, p, bf16: bool = False):
     return s * y, cache
 
 
-def backward(A_off, p, cache, dz):
-    """Gradient of sum(dz * z) with respect to every parameter."""
+def backward(A_off, p, cache, dz, bf16: bool = False):
+    """Gradient of sum(dz * z) with respect to every parameter (chain rule
+    through forward(); bf16=True rounds the stored values named above)."""
+    rnd = _bf if bf16 else (lambda x: x)
     s, rt = cache["s"], cache["rt"]
     dy = s * np.asarray(dz, dtype=np.float64)
     L = p["Ws"].shape[0]
+    Ws, Wm, wo = rnd(p["Ws"]), rnd(p["Wm"]), rnd(p["wo"])
     hL = cache["h"][L]
     grads = {"omega_j": np.array(rt @ dy), "wo": hL.T @ dy}
-    dh = np.outer(dy, p["wo"])
+    dh = np.outer(dy, wo)
     dWs = np.zeros_like(p["Ws"])
     dWm = np.zeros_like(p["Wm"])
     db = np.zeros_like(p["b"])
     for l in range(L - 1, -1, -1):
-        dp = dh * (cache["p"][l + 1] > 0)
+        dp = rnd(dh * (cache["p"][l + 1] > 0))
         h_prev, g = cache["h"][l], cache["g"][l]
         dWs[l] = dp.T @ h_prev
         dWm[l] = dp.T @ g
         db[l] = dp.sum(axis=0)
-        dh = dp @ p["Ws"][l] + A_off.T @ (dp @ p["Wm"][l])
-    dp0 = dh * (cache["p"][0] > 0)
+        dh = dp @ Ws[l] + A_off.T @ rnd(dp @ Wm[l])
+    dp0 = rnd(dh * (cache["p"][0] > 0))
     grads["e"] = dp0.T @ rt
     grads["b0"] = dp0.sum(axis=0)
     grads["Ws"], grads["Wm"], grads["b"] = dWs, dWm, db
     return grads
 
 
-def loss_and_grad(A_off, p, R, E):
+def loss_and_grad(A_off, p, R, E, bf16: bool = False):
     """Mean over samples of ||M_theta(r) - e||^2 / ||e||^2 and its gradient.
     R, E: (samples, n) residuals and corrections e = A^-1 r."""
     P = R.shape[0]
     total = 0.0
     grads = None
     for k in range(P):
-        z, cache = forward(A_off, R[k], p)
+        z, cache = forward(A_off, R[k], p, bf16=bf16)
         den = float(E[k] @ E[k])
         d = z - E[k]
         total += float(d @ d) / den / P
-        gk = backward(A_off, p, cache, 2.0 * d / den / P)
+        gk = backward(A_off, p, cache, 2.0 * d / den / P, bf16=bf16)
         grads = gk if grads is None else {key: grads[key] + gk[key] for key in grads}
     return total, grads
 
 
-def loss_and_grad_residual(A, A_off, p, R):
+def loss_and_grad_residual(A, A_off, p, R, bf16: bool = False):
     """Mean over samples of ||A M_theta(r) - r||^2 / ||r||^2 and its gradient
     (A: the full matrix, A_off: its off-diagonal graph for the net)."""
     P = R.shape[0]
     total = 0.0
     grads = None
     for k in range(P):
-        z, cache = forward(A_off, R[k], p)
+        z, cache = forward(A_off, R[k], p, bf16=bf16)
         den = float(R[k] @ R[k])
         t = A @ z - R[k]
         total += float(t @ t) / den / P
-        gk = backward(A_off, p, cache, 2.0 * (A.T @ t) / den / P)
+        gk = backward(A_off, p, cache, 2.0 * (A.T @ t) / den / P, bf16=bf16)
         grads = gk if grads is None else {key: grads[key] + gk[key] for key in grads}
     return total, grads

@@ -102,3 +102,19 @@ def test_bf16_forward_close_to_fp64():
     z, _ = LM.forward(A, r, p)
     zb, _ = LM.forward(A, r, p, bf16=True)
     assert np.linalg.norm(zb - z) <= 3e-2 * np.linalg.norm(z)
+
+
+def test_bf16_gradient_close_to_exact():
+    """The bf16-storage backward (the reference the GPU gradients are compared
+    with) stays within bf16 rounding of the exact gradient, per tensor."""
+    prob, A = _graph(N=6, seed=604)
+    p = LI.init_params(readout_scale=0.5)
+    R = rng.normal(8, 1, 2 * prob.n).reshape(2, prob.n)
+    E = rng.normal(9, 1, 2 * prob.n).reshape(2, prob.n)
+    _, g = LM.loss_and_grad(A, p, R, E)
+    _, gb = LM.loss_and_grad(A, p, R, E, bf16=True)
+    for k in LI.PARAM_ORDER:
+        a, b = np.ravel(gb[k]), np.ravel(g[k])
+        assert a @ b >= 0.99 * np.linalg.norm(a) * np.linalg.norm(b), k
+        assert np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(b) + 1e-12, k
+        assert not np.array_equal(a, b) or np.linalg.norm(b) == 0, k
