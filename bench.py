@@ -136,6 +136,14 @@ def _m_is_identity(s):
     return bool(np.all(m == one))
 
 
+def _config(args, prob, ws):
+    """The workload description both arms print (same keys, same values)."""
+    return {"workload": args.workload, "desc": WORKLOADS[args.workload], "solver": args.kind,
+            "n": prob.n, "nnz": prob.nnz, "tol": 1e-9, "parallelism": "replicas" if ws > 1 else "1 gpu",
+            "l2": "flushed (256 MiB write) before every timed solve",
+            "fuse_cgs": args.fuse_cgs, "fuse_step": args.fuse_step}
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -155,27 +163,31 @@ def replica_max(value, device):
 
 
 def cpu_baseline(prob, kind, outer_iters, max_seconds=25.0):
-    """The oracle as it stands, timed on this host's cores on a bounded sample:
-    whole outer iterations of the same solve (x0 = 0), scaled to the number of
-    outer iterations the full solve takes."""
+    """The oracle as it stands, timed on this host's cores on a bounded sample
+    of the same solve (x0 = 0): the first outer iteration alone (t1), then the
+    first k (tk) with k as large as the time budget allows.  The iterations not
+    run are charged at the marginal cost (tk - t1) / (k - 1) of iterations 2..k,
+    which carries the outer Gram-Schmidt's growth with the iteration index
+    (later iterations cost more than the first)."""
     import oracle as O
     P = O.Problem(prob, diag_scale=1)
-    prm = O.preset(kind)
-    k = 1
     t0 = time.perf_counter()
-    res = P.solve(O.preset(kind, max_outer=k), prob.b)
-    dt = time.perf_counter() - t0
-    per_iter = dt / max(1, res.outer_iters)
-    if per_iter * 2 < max_seconds and outer_iters > 1:
-        k = max(1, min(outer_iters, int(max_seconds / per_iter)))
-        t0 = time.perf_counter()
-        res = P.solve(O.preset(kind, max_outer=k), prob.b)
-        dt = time.perf_counter() - t0
-        per_iter = dt / max(1, res.outer_iters)
-    del prm
-    return {"value": per_iter * outer_iters * 1e3, "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{res.outer_iters} of {outer_iters} outer iterations of the same solve "
-                      f"({dt:.1f} s), scaled linearly to the full solve"}
+    r1 = P.solve(O.preset(kind, max_outer=1), prob.b)
+    t1 = time.perf_counter() - t0
+    k = max(1, min(outer_iters, int(max_seconds / max(t1, 1e-9))))
+    if k <= 1 or outer_iters <= 1:
+        return {"value": t1 * outer_iters * 1e3, "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+                "sample": f"1 of {outer_iters} outer iterations ({t1:.1f} s), scaled linearly"}
+    t0 = time.perf_counter()
+    rk = P.solve(O.preset(kind, max_outer=k), prob.b)
+    tk = time.perf_counter() - t0
+    k = rk.outer_iters
+    marg = (tk - t1) / max(1, k - r1.outer_iters)
+    value = tk + (outer_iters - k) * marg
+    return {"value": value * 1e3, "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{k} of {outer_iters} outer iterations of the same solve ({tk:.1f} s; the first alone "
+                      f"{t1:.1f} s); the other {outer_iters - k} charged at the marginal cost of iterations "
+                      f"2..{k} ({marg:.2f} s each)"}
 
 
 def level_error_report(prob, rp, ci, va, ds, dev, stream):
@@ -370,6 +382,9 @@ def run_learned(args):
                       "loss": args.learned_loss},
            "learned": out["learned"], "jacobi": out["jacobi"],
            "speedup_vs_jacobi": out["jacobi"]["ms"] / out["learned"]["ms"],
+           # the target: learned M reaches the same 1e-9 faster than Jacobi-F3R
+           "target_met": bool(out["learned"]["status"] == "OK" and out["jacobi"]["status"] == "OK"
+                              and out["learned"]["ms"] < out["jacobi"]["ms"]),
            "apply_quality": quality,
            "train": {"loss": args.learned_loss, "loss_initial": loss0, "loss_final": loss1, "loss_hist_first_last": [float(hist[0]), float(hist[-1])],
                      "train_ms": t_train, "pairs_s": t_pairs}}
@@ -453,15 +468,18 @@ def run_reference(args):
             steps.append(dt / max(1, res.outer_iters))
     per_iter = statistics.median(steps)
     value = per_iter * outer * 1e3
+    sample = (f"each step = the first outer iteration of the solve from x0 = 0 (median of {args.steps} "
+              f"steps, {per_iter:.2f} s each); value = that time x the oracle's {outer} outer iterations "
+              f"to 1e-9 (tests/golden/oracle_solves.json)")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64 (emulated on the CPU)",
-        "data": "synthetic", "config": {"workload": args.workload, "solver": args.kind, "n": prob.n,
-                                        "nnz": prob.nnz, "tol": 1e-9, "parallelism": "replicas"},
+        "data": "synthetic", "config": _config(args, prob, ws),
+        "extrapolated": {"outer_iters_to_solution": outer, "ms_per_outer_iter": per_iter * 1e3,
+                         "value_ms": value},
         "cpu_baseline": {"value": value, "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
-                         "sample": f"each step = 1 outer iteration of the solve (median of {args.steps}); "
-                                   f"scaled by the oracle's {outer} outer iterations to convergence"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
@@ -599,18 +617,31 @@ def main():
     ys = torch.empty(n, device=dev, dtype=torch.float32)
     for _ in range(5):
         s.spmv(sp_prec, f3r.F32, xs, ys, stream=stream)
-    reps = 50
+    sp_bytes = (isz + asz) * nnz + rsb + 4 * n + 4 * n
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cold = []
+    for _ in range(20):  # cold: L2 flushed (256 MiB write) before each launch, one launch per event pair
+        flush.fill_(2.0)
+        e0.record(stream)
+        s.spmv(sp_prec, f3r.F32, xs, ys, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        cold.append(e0.elapsed_time(e1) * 1e3)
+    sp_us = statistics.median(cold)
+    reps = 50
     flush.fill_(2.0)
     e0.record(stream)
     for _ in range(reps):
         s.spmv(sp_prec, f3r.F32, xs, ys, stream=stream)
     e1.record(stream)
     e1.synchronize()
-    sp_us = e0.elapsed_time(e1) * 1e3 / reps
-    sp_bytes = (isz + asz) * nnz + rsb + 4 * n + 4 * n
+    b2b_us = e0.elapsed_time(e1) * 1e3 / reps
     spmv = {"achieved": sp_bytes / (sp_us * 1e-6) / 1e9, "avg_launch_us": sp_us, "unit": "GB/s",
-            "algorithmic_bytes_per_launch": sp_bytes}
+            "algorithmic_bytes_per_launch": sp_bytes,
+            "l2": "flushed (256 MiB write) before each timed launch; median of 20 launches",
+            "back_to_back_us": b2b_us,
+            "back_to_back_note": f"{reps} launches on the same x and y after one flush: the working set "
+                                 "fits in L2, so later launches read from it"}
     spmv["frac"] = spmv["achieved"] / hbm
 
     # ---- per-level error of the low-precision levels against the fp64 path (same inputs)
@@ -619,7 +650,7 @@ def main():
     # ---- comparators on the same GPU (one solve each)
     comparators = {}
     if not args.no_comparators:
-        for kind in ("fp32-F3R", "fgmres64"):
+        for kind in ("fp32-F3R", "fp64-F3R", "fgmres64"):
             cp = f3r.preset(kind, diag_scale=ds)
             sc = f3r.Solver(rp, ci, va, cp, stream=stream)
             xc = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -647,10 +678,18 @@ def main():
             comparators[method] = {"ms": e0.elapsed_time(e1), "iters": rc.outer_iters,
                                    "status": f3r.STATUS.get(rc.status), "rel_res": rc.rel_res_true}
             del xc
-        comparators["speedup_vs_fgmres64"] = comparators["fgmres64"]["ms"] / ms_per_solve
-        comparators["speedup_vs_fp32_f3r"] = comparators["fp32-F3R"]["ms"] / ms_per_solve
-        comparators["speedup_vs_cg"] = comparators["cg"]["ms"] / ms_per_solve
-        comparators["speedup_vs_bicgstab"] = comparators["bicgstab"]["ms"] / ms_per_solve
+        # a speed-up is a ratio of times to the same residual: none against a
+        # comparator that stopped without reaching it
+        for key, kind in (("fgmres64", "fgmres64"), ("fp64_f3r", "fp64-F3R"), ("fp32_f3r", "fp32-F3R"),
+                          ("cg", "cg"), ("bicgstab", "bicgstab")):
+            c = comparators[kind]
+            conv = c["status"] == "OK"
+            comparators[f"speedup_vs_{key}"] = c["ms"] / ms_per_solve if conv else None
+            if not conv:
+                comparators[f"speedup_vs_{key}_note"] = (
+                    f"{kind} did not reach {1e-9:g} (status {c['status']}, relative residual "
+                    f"{c['rel_res']:.2e} after {c.get('outer_iters', c.get('iters'))} iterations, "
+                    f"{c['ms']:.0f} ms): no time-to-solution ratio")
 
     # ---- end to end through the C ABI with host buffers (setup + solve + result)
     rp_h = torch.from_numpy(prob.rowptr).pin_memory()
@@ -677,10 +716,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload], "solver": args.kind,
-                   "n": n, "nnz": nnz, "tol": 1e-9, "parallelism": "replicas" if ws > 1 else "1 gpu",
-                   "l2": "flushed (256 MiB write) before every timed solve",
-                   "fuse_cgs": args.fuse_cgs, "fuse_step": args.fuse_step},
+        "config": _config(args, prob, ws),
         "outer_iters": last.outer_iters, "rel_res_true": true_rel, "status": f3r.STATUS.get(last.status),
         "roofline": roofline, "spmv_fp16": spmv, "kernels": prof, "comparators": comparators,
         "level_errors": level_errors, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,

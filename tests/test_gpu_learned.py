@@ -1,6 +1,7 @@
 """Learned preconditioner M_theta on the GPU against the CPU oracle
-(oracle/learned.py): forward in bf16 storage, gradients, training and use as
-M inside the fp16 Richardson level."""
+(oracle/learned.py): forward in bf16 storage, gradients (against the oracle's
+backward with the same bf16 storage points: cosine >= 0.999 and 2e-2 relative
+per tensor), training and use as M inside the fp16 Richardson level."""
 import numpy as np
 import pytest
 
@@ -68,13 +69,14 @@ def test_gradient_matches_oracle(setup):
     E = rng.normal(12, 7, 2 * prob.n).reshape(2, prob.n).astype(np.float32)
     loss, grad = s.learned_loss_grad(dev(R), dev(E))
     pf = LI.unflatten(flat.astype(np.float64))
-    want_loss, want = LM.loss_and_grad(A16, pf, R.astype(np.float64), E.astype(np.float64))
+    want_loss, want = LM.loss_and_grad(A16, pf, R.astype(np.float64), E.astype(np.float64), bf16=True)
     assert abs(loss - want_loss) <= 2e-2 * want_loss
     g = LI.unflatten(grad.astype(np.float64))
     for k in LI.PARAM_ORDER:
         a, b = np.ravel(g[k]), np.ravel(want[k])
-        assert _cos(a, b) >= 0.99, k
-        assert np.linalg.norm(a - b) <= 0.15 * np.linalg.norm(b) + 1e-6, k
+        print(f"{k}: cos {_cos(a, b):.6f}, rel {np.linalg.norm(a - b) / np.linalg.norm(b):.2e}")
+        assert _cos(a, b) >= 0.999, k
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-6, k
 
 
 def test_residual_loss_gradient_matches_oracle(setup):
@@ -93,13 +95,14 @@ def test_residual_loss_gradient_matches_oracle(setup):
     finally:
         s.learned_set_loss(0)
     pf = LI.unflatten(flat.astype(np.float64))
-    want_loss, want = LM.loss_and_grad_residual(A16full, A16, pf, R.astype(np.float64))
+    want_loss, want = LM.loss_and_grad_residual(A16full, A16, pf, R.astype(np.float64), bf16=True)
     assert abs(loss - want_loss) <= 2e-2 * want_loss
     g = LI.unflatten(grad.astype(np.float64))
     for k in LI.PARAM_ORDER:
         a, b = np.ravel(g[k]), np.ravel(want[k])
-        assert _cos(a, b) >= 0.99, k
-        assert np.linalg.norm(a - b) <= 0.15 * np.linalg.norm(b) + 1e-6, k
+        print(f"{k}: cos {_cos(a, b):.6f}, rel {np.linalg.norm(a - b) / np.linalg.norm(b):.2e}")
+        assert _cos(a, b) >= 0.999, k
+        assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-6, k
 
 
 def test_training_reduces_loss_and_solves(setup):

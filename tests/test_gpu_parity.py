@@ -221,7 +221,13 @@ def test_inner_level_call(convdiff, kind, level, fuse):
     want = P.apply(_orc_prm(kind), O.rich_state(c_ntr=2), level, vt.astype(np.float64))
     got = z.cpu().numpy().astype(np.float64)
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
-    tol = {"fp64": 1e-12, "fp32": 1e-4, "fp16": 2e-2, "bf16": 5e-2}[kind]
+    # GPU and oracle differ only in the summation order of dot products (tree
+    # vs sequential: ~sqrt(n) u32 relative), amplified by the level's small
+    # least-squares solve; at the 16-bit levels that perturbation moves a
+    # fraction ~ (perturbation / u) of the entries cast to 16 bits by one ulp
+    # each (u16 = 2^-11, u_bf = 2^-8), a level-output change of order 1e-4.
+    # Bounds: fp16 10 u16, bf16 2.5 u_bf.
+    tol = {"fp64": 1e-12, "fp32": 1e-4, "fp16": 10 * 2.0 ** -11, "bf16": 2.5 * 2.0 ** -8}[kind]
     print(f"level {level} {kind}: rel diff {err:.3e}")
     assert err <= tol
 
