@@ -683,7 +683,7 @@ def main():
         for key, kind in (("fgmres64", "fgmres64"), ("fp64_f3r", "fp64-F3R"), ("fp32_f3r", "fp32-F3R"),
                           ("cg", "cg"), ("bicgstab", "bicgstab")):
             c = comparators[kind]
-            conv = c["status"] == "OK"
+            conv = c["status"] == f3r.STATUS[f3r.OK]
             comparators[f"speedup_vs_{key}"] = c["ms"] / ms_per_solve if conv else None
             if not conv:
                 comparators[f"speedup_vs_{key}_note"] = (

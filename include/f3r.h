@@ -172,9 +172,24 @@ f3r_status f3r_set_rich_state(f3r_ctx *ctx, const double *omega8, int64_t c_ntr)
  * 5 row scales (float, n); 6 M in m_prec (n elements of that precision);
  * approximate inverse (F3R_PC_AINV), fp16 bits: 7 L Dt^-1 (nnz, zero off the
  * strict lower triangle), 8 Dt^-1 U (nnz, zero off the strict upper
- * triangle), 9 Dt^-1 (n).
+ * triangle), 9 Dt^-1 (n); 10 (windowed matrices, see f3r_matrix_info) the
+ * column each entry's 16-bit window index stands for (int32, nnz: equal to
+ * colidx when the set-up is right).
  * Returns F3R_ERR_ARG if the array does not exist. */
 f3r_status f3r_export(f3r_ctx *ctx, int which, void *out);
+
+/* Storage of the set-up matrix (instrumentation), out[8]:
+ *   [0] 1 if the matrix is windowed (below), [1] largest window of a tile
+ *   (entries), [2] stored SELL entries (padding included), [3] widest slice,
+ *   [4] slices of 32 rows, [5] bytes per stored column index (2 windowed,
+ *   4 otherwise), [6] window chunk (entries), [7] 1 if every entry of M is 1.
+ * Windowed: the columns of every 256-row tile lie in at most 14 runs of x
+ * (4096 entries in all) that the kernels bulk-copy into shared memory with
+ * the tile's SELL slices (Sec. 5.2), and each entry stores a 16-bit index
+ * into that window instead of an int32 column.  Set up for every matrix
+ * whose tiles fit (banded and stencil matrices); otherwise the kernels
+ * gather x by int32 column from global memory.  Same results either way. */
+f3r_status f3r_matrix_info(f3r_ctx *ctx, int64_t *out);
 
 /* Kernel event profiler (instrumentation).  With enable = 1 the totals are
  * reset, every kernel the context launches is bracketed by two CUDA events

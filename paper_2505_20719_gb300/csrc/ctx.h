@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "stage.cuh"
 
 namespace f3r {
 
@@ -69,6 +70,12 @@ struct Ctx {
     int wmax = 0;              // widest slice (entries per row)
     long long nsell = 0;
     int *sptr = nullptr, *col = nullptr, *rowptr = nullptr;
+    // windowed tiles (stage.cuh): 16-bit window index per SELL entry and one
+    // record of x runs per 256-row tile; win = every tile fits its window
+    uint16_t *lcol = nullptr;
+    int *wrec = nullptr;
+    bool win = false;
+    int win_max = 0;            // largest window of any tile (entries)
     double *a64 = nullptr;      // original A
     double *ah64 = nullptr;     // scaled A^ in fp64
     float *a32 = nullptr;       // A^ in fp32
@@ -159,6 +166,10 @@ inline Sell sell_of(const Ctx &c) { return Sell{c.n, c.nslices, c.sptr, c.col}; 
 
 // setup.cu
 f3r_status build_matrix(Ctx &c, const int *rowptr_d, const int *colidx_d, const double *val_d, cudaStream_t s);
+// window.cu: windowed tiles of the SELL matrix (sets c.win); the Window a
+// kernel gathering x of xsize bytes (n entries) takes (empty when not windowed)
+f3r_status build_window(Ctx &c, cudaStream_t s);
+Window window_of(const Ctx &c, int xsize, int n);
 f3r_status export_array(Ctx &c, int which, void *out, cudaStream_t s);
 
 // launch_levels.cu
@@ -213,7 +224,9 @@ int prec_bytes(int p);
 struct StagePlan {
     int S = 0, stage_bytes = 0, smem = 0;
 };
-StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize);
+// xsize > 0: a windowed kernel gathering x of xsize bytes (sized for the
+// widest window; only meaningful when c.win)
+StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize, int xsize = 0);
 // stream-ordered device memory from the per-device pool (mem.cu)
 void *pool_alloc(int dev, size_t bytes, cudaStream_t s);
 // Raise the dynamic shared memory limit of a kernel to at least `bytes`,

@@ -141,31 +141,52 @@ template <class K> static int staged_grid(Ctx &c, K kern, int smem, int work_blo
     return std::max(1, std::min(c.nsm * nb, work_blocks));
 }
 
-template <class TA, class T, int S, int MAXD>
+template <class TA, class T, int S, int MAXD, bool WIN>
 static void spmv_dots_st_go(Ctx &c, int d, int j, const TA *val, const float *rs, const StagePlan &pl,
                             cudaStream_t s) {
-    auto kern = k_spmv_dots_st<TA, T, S, MAXD>;
+    auto kern = k_spmv_dots_st<TA, T, S, MAXD, WIN>;
     const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
     // block totals of hA for the fused CGS2 launch that follows, when it will run
     const bool defer = d >= 1 && d <= 3 && c.fplan[d].G > 0;
     c.hpart_G[d] = defer ? g : 0;
     launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots),
-                                    StageCfg{pl.stage_bytes, c.err}, defer ? (T *)c.hpart : (T *)nullptr);
+                                    StageCfg{pl.stage_bytes, c.err}, defer ? (T *)c.hpart : (T *)nullptr,
+                                    WIN ? window_of(c, sizeof(T), c.n) : Window());
+}
+
+template <class TA, class T, bool WIN>
+static bool spmv_dots_plan_go(Ctx &c, int d, int j, const TA *val, const float *rs, const StagePlan &pl,
+                              cudaStream_t s) {
+    const int md = maxd_bucket(c.L[d].m);
+    if constexpr (WIN) {
+        if (pl.S == 4) {
+            if (md == 4) spmv_dots_st_go<TA, T, 4, 4, WIN>(c, d, j, val, rs, pl, s);
+            else if (md == 8) spmv_dots_st_go<TA, T, 4, 8, WIN>(c, d, j, val, rs, pl, s);
+            else spmv_dots_st_go<TA, T, 4, 16, WIN>(c, d, j, val, rs, pl, s);
+            return true;
+        }
+    }
+    if (pl.S == 3) {
+        if (md == 4) spmv_dots_st_go<TA, T, 3, 4, WIN>(c, d, j, val, rs, pl, s);
+        else if (md == 8) spmv_dots_st_go<TA, T, 3, 8, WIN>(c, d, j, val, rs, pl, s);
+        else spmv_dots_st_go<TA, T, 3, 16, WIN>(c, d, j, val, rs, pl, s);
+        return true;
+    }
+    if (pl.S == 2) {
+        if (md == 4) spmv_dots_st_go<TA, T, 2, 4, WIN>(c, d, j, val, rs, pl, s);
+        else if (md == 8) spmv_dots_st_go<TA, T, 2, 8, WIN>(c, d, j, val, rs, pl, s);
+        else spmv_dots_st_go<TA, T, 2, 16, WIN>(c, d, j, val, rs, pl, s);
+        return true;
+    }
+    return false;
 }
 
 template <class TA, class T>
 static void spmv_dots_go(Ctx &c, int d, int j, const TA *val, const float *rs, cudaStream_t s) {
+    if (c.win && spmv_dots_plan_go<TA, T, true>(c, d, j, val, rs, plan_stage(c, sizeof(TA), c.L[d].m, sizeof(T), sizeof(T)), s))
+        return;
     const StagePlan pl = plan_stage(c, sizeof(TA), c.L[d].m, sizeof(T));
-    const int md = maxd_bucket(c.L[d].m);
-    if (pl.S == 3) {
-        if (md == 4) spmv_dots_st_go<TA, T, 3, 4>(c, d, j, val, rs, pl, s);
-        else if (md == 8) spmv_dots_st_go<TA, T, 3, 8>(c, d, j, val, rs, pl, s);
-        else spmv_dots_st_go<TA, T, 3, 16>(c, d, j, val, rs, pl, s);
-    } else if (pl.S == 2) {
-        if (md == 4) spmv_dots_st_go<TA, T, 2, 4>(c, d, j, val, rs, pl, s);
-        else if (md == 8) spmv_dots_st_go<TA, T, 2, 8>(c, d, j, val, rs, pl, s);
-        else spmv_dots_st_go<TA, T, 2, 16>(c, d, j, val, rs, pl, s);
-    } else {
+    if (!spmv_dots_plan_go<TA, T, false>(c, d, j, val, rs, pl, s)) {
         c.hpart_G[d] = 0;
         launch_pdl(k_spmv_dots<TA, T>, dim3(c.Gs), dim3(kBlock), 0, s, sell_of(c), val, rs, levdev<T>(c, d), j, gred<T>(c, kMaxDots));
     }
@@ -286,16 +307,33 @@ __global__ void __launch_bounds__(kBlock) k_outer_store_z(LevelDev<double> L, co
 bool launch_outer_step(Ctx &c, cudaStream_t s) {
     LevelDev<double> L = levdev<double>(c, 0);
     prof_begin(c, PK_OUTER_SPMV, 0, s);
+    const StagePlan pw = c.win ? plan_stage(c, sizeof(double), 0, 8, sizeof(double)) : StagePlan();
     const StagePlan pl = plan_stage(c, sizeof(double), 0, 8);
-    if (pl.S == 3) {
+    const Window wn = window_of(c, sizeof(double), c.n);
+    if (pw.S == 4) {
+        auto kern = k_outer_spmv_st<4, true>;
+        const int g = staged_grid(c, kern, pw.smem, ceil_div(c.nslices, kTileSlices));
+        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pw.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pw.stage_bytes, c.err}, wn);
+        c.launches--;
+    } else if (pw.S == 3) {
+        auto kern = k_outer_spmv_st<3, true>;
+        const int g = staged_grid(c, kern, pw.smem, ceil_div(c.nslices, kTileSlices));
+        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pw.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pw.stage_bytes, c.err}, wn);
+        c.launches--;
+    } else if (pw.S == 2) {
+        auto kern = k_outer_spmv_st<2, true>;
+        const int g = staged_grid(c, kern, pw.smem, ceil_div(c.nslices, kTileSlices));
+        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pw.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pw.stage_bytes, c.err}, wn);
+        c.launches--;
+    } else if (pl.S == 3) {
         auto kern = k_outer_spmv_st<3>;
         const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
-        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err});
+        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err}, Window());
         c.launches--;
     } else if (pl.S == 2) {
         auto kern = k_outer_spmv_st<2>;
         const int g = staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices));
-        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err});
+        launch_pdl(kern, dim3(g), dim3(kStagedThreads), pl.smem, s, sell_of(c), c.a64, L, (const double *)c.zst, StageCfg{pl.stage_bytes, c.err}, Window());
         c.launches--;
     } else {
         launch_pdl(k_outer_store_z, dim3(c.G), dim3(kBlock), 0, s, L, (const double *)c.zst);
@@ -356,16 +394,34 @@ __global__ void __launch_bounds__(kBlock) k_spmv(Sell S, const TA *__restrict__ 
 
 template <class TA, class TX, class TY>
 static void spmv_go(Ctx &c, const TA *val, const float *rs, const TX *x, TY *y, cudaStream_t s) {
+    // the window's bulk copies read x from 16-byte aligned addresses (a caller's
+    // x at another offset is gathered from global memory instead)
+    const bool xal = ((uintptr_t)x % 16) == 0;
+    const StagePlan pw = (c.win && xal) ? plan_stage(c, sizeof(TA), 0, 4, sizeof(TX)) : StagePlan();
     const StagePlan pl = plan_stage(c, sizeof(TA), 0, 4);
     const StageCfg cfg{pl.stage_bytes, c.err};
-    if (pl.S == 3) {
+    const StageCfg cfw{pw.stage_bytes, c.err};
+    const int work = ceil_div(c.nslices, kTileSlices);
+    if (pw.S == 4) {
+        auto kern = k_spmv_st<TA, TX, TY, 4, true>;
+        launch_pdl(kern, dim3(staged_grid(c, kern, pw.smem, work)), dim3(kStagedThreads), pw.smem, s, sell_of(c), val, rs, x, y,
+                   cfw, window_of(c, sizeof(TX), c.n));
+    } else if (pw.S == 3) {
+        auto kern = k_spmv_st<TA, TX, TY, 3, true>;
+        launch_pdl(kern, dim3(staged_grid(c, kern, pw.smem, work)), dim3(kStagedThreads), pw.smem, s, sell_of(c), val, rs, x, y,
+                   cfw, window_of(c, sizeof(TX), c.n));
+    } else if (pw.S == 2) {
+        auto kern = k_spmv_st<TA, TX, TY, 2, true>;
+        launch_pdl(kern, dim3(staged_grid(c, kern, pw.smem, work)), dim3(kStagedThreads), pw.smem, s, sell_of(c), val, rs, x, y,
+                   cfw, window_of(c, sizeof(TX), c.n));
+    } else if (pl.S == 3) {
         auto kern = k_spmv_st<TA, TX, TY, 3>;
-        launch_pdl(kern, dim3(staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices))), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs,
-                                                                                                x, y, cfg);
+        launch_pdl(kern, dim3(staged_grid(c, kern, pl.smem, work)), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs,
+                                                                                                x, y, cfg, Window());
     } else if (pl.S == 2) {
         auto kern = k_spmv_st<TA, TX, TY, 2>;
-        launch_pdl(kern, dim3(staged_grid(c, kern, pl.smem, ceil_div(c.nslices, kTileSlices))), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs,
-                                                                                                x, y, cfg);
+        launch_pdl(kern, dim3(staged_grid(c, kern, pl.smem, work)), dim3(kStagedThreads), pl.smem, s, sell_of(c), val, rs,
+                                                                                                x, y, cfg, Window());
     } else {
         launch_pdl(k_spmv<TA, TX, TY>, dim3(c.Gs), dim3(kBlock), 0, s, sell_of(c), val, rs, x, y);
     }

@@ -33,20 +33,35 @@ static void rich_go(Ctx &c, const TA *val, bool update, int pos, TP *out, const 
     if (!update) {
         if (m4 == 2) {
             prof_begin(c, PK_RICH2, 0, s);
+            const StagePlan pw = (c.win && c.m_unit) ? plan_stage(c, sizeof(TA), 0, 4, sizeof(VS)) : StagePlan();
             const StagePlan pl = plan_stage(c, sizeof(TA), 0, 4);
             const StageCfg cfg{pl.stage_bytes, c.err};
-            if (pl.S == 3 && c.m_unit) {
+            const StageCfg cfw{pw.stage_bytes, c.err};
+            const Window wn = window_of(c, sizeof(VS), n);
+            if (pw.S == 4) {
+                auto kern = k_rich2_st<TA, VS, TC, TP, 4, true, true>;
+                launch_pdl(kern, dim3(rich_grid(c, kern, pw.smem)), dim3(kStagedThreads), pw.smem, s, S, val, rs, v, mv, out,
+                           par_misc, R, c.flags, cd, n, cfw, wn);
+            } else if (pw.S == 3) {
+                auto kern = k_rich2_st<TA, VS, TC, TP, 3, true, true>;
+                launch_pdl(kern, dim3(rich_grid(c, kern, pw.smem)), dim3(kStagedThreads), pw.smem, s, S, val, rs, v, mv, out,
+                           par_misc, R, c.flags, cd, n, cfw, wn);
+            } else if (pw.S == 2) {
+                auto kern = k_rich2_st<TA, VS, TC, TP, 2, true, true>;
+                launch_pdl(kern, dim3(rich_grid(c, kern, pw.smem)), dim3(kStagedThreads), pw.smem, s, S, val, rs, v, mv, out,
+                           par_misc, R, c.flags, cd, n, cfw, wn);
+            } else if (pl.S == 3 && c.m_unit) {
                 auto kern = k_rich2_st<TA, VS, TC, TP, 3, true>;
                 launch_pdl(kern, dim3(rich_grid(c, kern, pl.smem)), dim3(kStagedThreads), pl.smem, s, S, val, rs, v, mv, out, par_misc, R, c.flags,
-                                                                          cd, n, cfg);
+                                                                          cd, n, cfg, Window());
             } else if (pl.S == 3) {
                 auto kern = k_rich2_st<TA, VS, TC, TP, 3>;
                 launch_pdl(kern, dim3(rich_grid(c, kern, pl.smem)), dim3(kStagedThreads), pl.smem, s, S, val, rs, v, mv, out, par_misc, R, c.flags,
-                                                                          cd, n, cfg);
+                                                                          cd, n, cfg, Window());
             } else if (pl.S == 2) {
                 auto kern = k_rich2_st<TA, VS, TC, TP, 2>;
                 launch_pdl(kern, dim3(rich_grid(c, kern, pl.smem)), dim3(kStagedThreads), pl.smem, s, S, val, rs, v, mv, out, par_misc, R, c.flags,
-                                                                          cd, n, cfg);
+                                                                          cd, n, cfg, Window());
             } else {
                 launch_pdl(k_rich2<TA, VS, TC, TP>, dim3(c.Gs), dim3(kBlock), 0, s, S, val, rs, v, mv, out, par_misc, R, c.flags, cd, n);
             }

@@ -172,6 +172,25 @@ __global__ void k_export(const int *rp, int n, const int *sptr, const S *src, S 
     }
 }
 
+// windowed tiles: the column each entry's window index stands for, in CSR
+// order (the tile's runs concatenated in column order)
+__global__ void k_export_win(const int *rp, int n, const int *sptr, const uint16_t *lcol, const int *rec, int *dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int s = i / kSlice, lane = i % kSlice;
+        const int *r = rec + (size_t)(i / kTileRows) * kWinRec;
+        const int b = rp[i], len = rp[i + 1] - b;
+        for (int k = 0; k < len; ++k) {
+            const int l = lcol[sptr[s] + lane + k * kSlice];
+            int c = -1;
+            for (int q = 0; q < r[0]; ++q) {
+                const int c0 = r[kWinRecRun + 3 * q], ln = r[kWinRecRun + 3 * q + 1], pos = r[kWinRecRun + 3 * q + 2];
+                if (l >= pos && l < pos + ln) c = c0 + (l - pos);
+            }
+            dst[b + k] = c;
+        }
+    }
+}
+
 static void *dalloc(Ctx &c, size_t bytes) {
     if (bytes == 0) bytes = 16;
     void *p = pool_alloc(c.dev, bytes, c.zstream);
@@ -270,7 +289,7 @@ f3r_status build_matrix(Ctx &c, const int *rp, const int *ci, const double *val,
     if (cudaStreamSynchronize(s) != cudaSuccess) return F3R_ERR_CUDA;
     const char *e = getenv("F3R_UNIT_M");  // 0: keep loading M (for the bit-identity test)
     c.m_unit = (nonunit_h == 0) && !(e && e[0] == '0');
-    return F3R_OK;
+    return build_window(c, s);
 }
 
 f3r_status export_array(Ctx &c, int which, void *out, cudaStream_t s) {
@@ -327,6 +346,12 @@ f3r_status export_array(Ctx &c, int which, void *out, cudaStream_t s) {
             if (!c.ainv_dinv) return F3R_ERR_ARG;
             cudaMemcpyAsync(out, c.ainv_dinv, sizeof(h16) * n, cudaMemcpyDeviceToHost, s);
             return cudaStreamSynchronize(s) == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
+        case 10:
+            if (!c.win) return F3R_ERR_ARG;
+            bytes = sizeof(int) * (size_t)c.nnz;
+            if (cudaMalloc(&tmp, bytes ? bytes : 16) != cudaSuccess) return F3R_ERR_NOMEM;
+            k_export_win<<<grid, kBlock, 0, s>>>(c.rowptr, n, c.sptr, c.lcol, c.wrec, (int *)tmp);
+            break;
         default:
             return F3R_ERR_ARG;
     }
@@ -337,19 +362,27 @@ f3r_status export_array(Ctx &c, int which, void *out, cudaStream_t s) {
     return e == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
 }
 
-StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize) {
+StagePlan plan_stage(const Ctx &c, int asize, int n_extra, int esize, int xsize) {
     StagePlan p;
     if (!c.staged) return p;
-    const int sb = stage_bytes_for(c.wmax, asize, n_extra, esize);
+    const bool win = c.win && xsize > 0;
+    const int sb = stage_bytes_for(c.wmax, asize, n_extra, esize, win ? c.win_max : 0, win ? xsize : 0);
     // 3 stages if four blocks fit an SM, else 2 stages with two blocks, else
-    // 2 stages with one block; wider tiles run unstaged.
+    // 2 stages with one block; wider tiles run unstaged.  Windowed kernels
+    // (smaller stages) may take 4 stages.
     static const int force_s = [] {
         const char *e = getenv("F3R_STAGES");  // 2 or 3: ring depth override for tuning runs
         return e ? atoi(e) : 0;
     }();
-    const int cand[3][2] = {{3, 56 * 1024}, {2, 110 * 1024}, {2, 220 * 1024}};
+    static const int win_s = [] {
+        const char *e = getenv("F3R_WSTAGES");  // 2, 3 or 4: ring depth of windowed kernels (tuning)
+        const int v = e ? atoi(e) : 0;
+        return (v >= 2 && v <= 4) ? v : kWinStages;
+    }();
+    const int cand[4][2] = {{4, 56 * 1024}, {3, 56 * 1024}, {2, 110 * 1024}, {2, 220 * 1024}};
     for (auto &cs : cand) {
-        if (force_s == 2 && cs[0] == 3) continue;
+        if (cs[0] == 4 && !(win && win_s == 4)) continue;
+        if (cs[0] == 3 && (force_s == 2 || (win && win_s == 2))) continue;
         const int smem = 256 + cs[0] * sb;
         if (smem <= cs[1]) {
             p.S = cs[0];

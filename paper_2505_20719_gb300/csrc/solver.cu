@@ -795,4 +795,18 @@ f3r_status f3r_export(f3r_ctx *h, int which, void *out) {
     return export_array(h->c, which, out, h->cs);
 }
 
+f3r_status f3r_matrix_info(f3r_ctx *h, int64_t *out) {
+    if (!h || !out) return F3R_ERR_ARG;
+    const Ctx &c = h->c;
+    out[0] = c.win ? 1 : 0;
+    out[1] = c.win_max;
+    out[2] = c.nsell;
+    out[3] = c.wmax;
+    out[4] = c.nslices;
+    out[5] = c.win ? 2 : 4;
+    out[6] = kWinChunk;
+    out[7] = c.m_unit ? 1 : 0;
+    return F3R_OK;
+}
+
 }  // extern "C"

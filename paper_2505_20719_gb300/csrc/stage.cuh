@@ -47,6 +47,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// raise the barrier's expected transaction bytes without arriving (the
+// phase cannot complete before the arrive that follows)
+__device__ __forceinline__ void mbar_expect_tx_only(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
 // global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile(
@@ -117,21 +123,58 @@ struct Extra {
 
 constexpr int kTileSlices = kWarps;              // one slice per warp of the block
 constexpr int kTileRows = kTileSlices * kSlice;  // 256 rows per tile
+
+// Windowed tiles.  The columns the rows of one tile reference, and the
+// tile's own rows, are covered by at most kWinRuns runs of consecutive x
+// entries that start and end on kWinChunk-entry boundaries; the producer
+// bulk-copies those runs of x into the stage after the tile's matrix and
+// zeroes the 16 bytes just past them (the zero slot), and the tile's entries
+// carry 16-bit indices into that window instead of int32 columns, so the
+// consumers gather x from shared memory.  A padding entry (value +0) points
+// at the zero slot: it adds +0 * +0 to its row sum, which leaves every sum
+// bit for bit as it was (a sum that starts at +0 never becomes -0 under
+// round-to-nearest, and x + (+0) = x for every other x), so no entry needs a
+// test.  Per tile a record of kWinRec ints: [runs, window entries, 1 if a
+// run reaches past the last row of x (else 0), window index of the tile's
+// first row, then (first column, entries, window position) per run].
+constexpr int kWinChunk = 32;
+constexpr int kWinRuns = 9;
+constexpr int kWinRec = 32;
+constexpr int kWinRecClamp = 2;
+constexpr int kWinRecOwn = 3;
+constexpr int kWinRecRun = 4;  // run r at kWinRecRun + 3 r
+constexpr int kWinMaxEntries = 4096;
+constexpr int kWinPadBytes = 16;  // the zero slot after the window
+constexpr int kWinStages = 3;     // ring depth of the windowed kernels
+
+struct Window {
+    const uint16_t *lcol = nullptr;  // window index of every SELL entry (padding: the zero slot)
+    const int *rec = nullptr;        // kWinRec ints per tile
+    const void *x = nullptr;         // the gathered vector
+    int xsize = 0;                   // its element size (2, 4 or 8 bytes)
+    int n = 0;                       // its entries (runs are clamped to them)
+};
 // stage header: the tile's kTileSlices + 1 slice offsets (int), padded to a
-// multiple of 16 bytes so the bulk copies after it stay aligned
-constexpr int kStageHdr = ((kTileSlices + 1) * 4 + 15) / 16 * 16;
+// multiple of 16 bytes, then (windowed tiles) the tile's window record, so the
+// bulk copies after it stay aligned
+constexpr int kStageOffs = ((kTileSlices + 1) * 4 + 15) / 16 * 16;
+constexpr int kStageHdr = kStageOffs + kWinRec * 4;
 
 // What one warp sees of its slice in a staged tile.
 template <class TA> struct StageView {
-    const int *col;     // 32 w entries, column-major within the slice
+    const int *col;     // 32 w entries, column-major within the slice (plain tiles)
+    const uint16_t *lcol;  // the same as window indices (windowed tiles)
     const TA *val;
     const char *extra;  // extra l of the whole tile at extra + l * 256 * esize
+    const char *win;    // the tile's x window (windowed tiles)
+    int own;            // window index of the tile's first row (windowed tiles)
     int w;
     int esize;
     int row0;           // row of lane 0 inside the tile (32 * warp)
     template <class T> __device__ const T *ext(int l) const {
         return reinterpret_cast<const T *>(extra + (size_t)l * kTileRows * esize) + row0;
     }
+    template <class T> __device__ const T *xwin() const { return reinterpret_cast<const T *>(win); }
 };
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -154,47 +197,129 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // running writes): it waits for the prerequisite grids and returns false
 // when the kernel has nothing to do; the producer then waits for the copies
 // it issued and the call returns false.
-template <class TA, int S, bool EVICT_FIRST = false, class Body, class Gate>
+// WIN: windowed tiles (16-bit window indices, Window wn).  The x window of a
+// tile is written by the grid the gate waits for, so its runs are copied
+// only after the gate: the first S tiles' matrix copies raise their stage's
+// expected bytes without arriving, and the window copies (plus the arrive)
+// follow the gate.  A run ending past the last 16-byte boundary of x is
+// copied in bulk up to that boundary and the rest entry by entry by the
+// producer lanes before the arrive.
+template <class TA, int S, bool EVICT_FIRST = false, bool WIN = false, class Body, class Gate>
 __device__ __forceinline__ bool staged_tiles_gated(const Sell &A, const TA *__restrict__ val, int tile_begin,
                                                    int tile_end, char *ring, int stage_bytes, uint64_t *full,
-                                                   uint64_t *empty, Extra ex, int *err, Body body, Gate gate) {
+                                                   uint64_t *empty, Extra ex, int *err, Body body, Gate gate,
+                                                   Window wn = Window()) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool producer = (warp == kWarps);
+    constexpr uint32_t kIdxBytes = WIN ? 2u : 4u;
+    // metadata of the next tile the producer issues, loaded one tile ahead so
+    // that no global-load latency sits between two tiles' copies: lanes
+    // 0..kTileSlices hold its slice offsets, lane q word q of its window record
+    int meta_off = 0, meta_rec = 0;
+    uint64_t policy = 0;  // L2 policy of the matrix copies (EVICT_FIRST)
+    if constexpr (EVICT_FIRST)
+        if (producer) policy = l2_evict_first_policy();
+    auto prefetch = [&](int t) {
+        if (t >= tile_end) return;
+        const int s0 = t * kTileSlices;
+        meta_off = (lane <= kTileSlices) ? __ldg(A.sptr + min(s0 + lane, min(s0 + kTileSlices, A.nslices))) : 0;
+        if constexpr (WIN) meta_rec = __ldg(wn.rec + (size_t)t * kWinRec + lane);
+    };
     // run by the whole producer warp: lanes 0..8 write the tile's slice
     // offsets into the stage header (the consumers read them from shared
-    // memory instead of global memory), lane 0 issues the bulk copies
-    auto issue = [&](int t, int st) {
-        const int s0 = t * kTileSlices;
-        const int s1 = min(s0 + kTileSlices, A.nslices);
+    // memory instead of global memory), all lanes its window record, then the
+    // next tile's metadata is requested; lane 0 issues the bulk copies of the
+    // matrix and the extras; with `arrive` false (windowed tiles) it only
+    // raises the expected bytes and issue_window arrives
+    auto issue = [&](int t, int st, bool arrive) {
         char *sbase = ring + (size_t)st * stage_bytes;
-        int off = 0;
-        if (lane <= kTileSlices) {
-            off = __ldg(A.sptr + min(s0 + lane, s1));
-            reinterpret_cast<int *>(sbase)[lane] = off;
-        }
+        const int off = meta_off;
+        if (lane <= kTileSlices) reinterpret_cast<int *>(sbase)[lane] = off;
+        if constexpr (WIN) reinterpret_cast<int *>(sbase + kStageOffs)[lane] = meta_rec;
+        prefetch(t + 1);
         const int b0 = __shfl_sync(0xffffffffu, off, 0), b1 = __shfl_sync(0xffffffffu, off, kTileSlices);
-        __syncwarp();  // the header before lane 0's arrive (release) on full[st]
-        if (lane != 0) return;
-        const uint32_t colb = (uint32_t)(b1 - b0) * 4u;
+        const uint32_t colb = (uint32_t)(b1 - b0) * kIdxBytes;
         const uint32_t valb = (uint32_t)(b1 - b0) * (uint32_t)sizeof(TA);
         const uint32_t extb = (uint32_t)kTileRows * ex.esize;
         const uint32_t bar = smem_u32(full + st);
         const uint32_t dst = smem_u32(sbase + kStageHdr);
-        fence_proxy_async();  // the consumers' generic reads of this stage before the async refill
-        mbar_expect_tx(bar, colb + valb + extb * ex.count);
-        if (colb) {
-            if constexpr (EVICT_FIRST) {
-                const uint64_t pol = l2_evict_first_policy();
-                bulk_g2s_hint(dst, A.col + b0, colb, bar, pol);
-                bulk_g2s_hint(dst + colb, val + b0, valb, bar, pol);
-            } else {
-                bulk_g2s(dst, A.col + b0, colb, bar);
-                bulk_g2s(dst + colb, val + b0, valb, bar);
-            }
+        __syncwarp();  // the header before lane 0's arrive (release) on full[st]
+        if (lane == 0) {
+            if (arrive) mbar_expect_tx(bar, colb + valb + extb * ex.count);
+            else mbar_expect_tx_only(bar, colb + valb + extb * ex.count);
         }
-        for (int l = 0; l < ex.count; ++l)
+        __syncwarp();  // the expected bytes raised before any copy can complete
+        // lane 0 copies the indices, lane 1 the values, lane 2 + l extra l
+        if (lane >= 2 + ex.count || (lane < 2 && colb == 0)) return;
+        fence_proxy_async();  // the consumers' generic reads of this stage before the async refill
+        if (lane < 2) {
+            const void *src;
+            if (lane == 0) {
+                if constexpr (WIN) src = wn.lcol + b0;
+                else src = A.col + b0;
+            } else {
+                src = val + b0;
+            }
+            const uint32_t d = dst + (lane == 0 ? 0u : colb), bytes = lane == 0 ? colb : valb;
+            if constexpr (EVICT_FIRST) bulk_g2s_hint(d, src, bytes, bar, policy);
+            else bulk_g2s(d, src, bytes, bar);
+        } else {
+            const int l = lane - 2;
             bulk_g2s(dst + colb + valb + l * extb,
                      (const char *)ex.base + ((size_t)l * ex.ld + (size_t)t * kTileRows) * ex.esize, extb, bar);
+        }
+    };
+    // windowed tiles, after issue(t, st, false) and the gate: the x runs of
+    // the tile in stage st (lane r + 1 copies run r), then the arrive on full[st]
+    auto issue_window = [&](int st) {
+        const char *sbase = ring + (size_t)st * stage_bytes;
+        const int *hdr = reinterpret_cast<const int *>(sbase);
+        const int *rec = reinterpret_cast<const int *>(sbase + kStageOffs);  // written by issue()
+        const int nruns = rec[0], entries = rec[1];
+        const int tile_nnz = hdr[kTileSlices] - hdr[0];
+        char *wdst = const_cast<char *>(sbase) + kStageHdr + (size_t)tile_nnz * (kIdxBytes + sizeof(TA)) +
+                     (size_t)ex.count * kTileRows * ex.esize;
+        // lane r owns run r: its first column, length and place in the window
+        int c0 = 0, len = 0, pos = 0;
+        if (lane < nruns) {
+            c0 = rec[kWinRecRun + 3 * lane];
+            len = rec[kWinRecRun + 3 * lane + 1];
+            pos = rec[kWinRecRun + 3 * lane + 2];
+        }
+        const uint32_t bar = smem_u32(full + st);
+        if (lane == 0)  // the zero slot padding entries read
+            *reinterpret_cast<uint4 *>(wdst + (size_t)entries * wn.xsize) = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t bytes;
+        if (rec[kWinRecClamp] == 0) {  // every run lies inside x: whole runs, known total
+            bytes = (uint32_t)len * (uint32_t)wn.xsize;
+            __syncwarp();  // the zero slot before lane 0's arrive (release)
+            if (lane == 0) mbar_expect_tx(bar, (uint32_t)entries * (uint32_t)wn.xsize);
+        } else {
+            // runs cut at the end of x: the part of a run inside x that ends on a
+            // 16-byte boundary in bulk, the rest entry by entry
+            const int have = max(0, min(len, wn.n - c0));
+            const int per16 = 16 / wn.xsize;
+            int bulk = have;
+            if (c0 + have == wn.n) bulk = have / per16 * per16;
+            for (int e = bulk; e < have; ++e) {
+                const char *src = (const char *)wn.x + (size_t)(c0 + e) * wn.xsize;
+                char *d = wdst + (size_t)(pos + e) * wn.xsize;
+                if (wn.xsize == 2) *reinterpret_cast<uint16_t *>(d) = *reinterpret_cast<const uint16_t *>(src);
+                else if (wn.xsize == 4) *reinterpret_cast<uint32_t *>(d) = *reinterpret_cast<const uint32_t *>(src);
+                else *reinterpret_cast<uint64_t *>(d) = *reinterpret_cast<const uint64_t *>(src);
+            }
+            bytes = (uint32_t)bulk * (uint32_t)wn.xsize;
+            uint32_t total = bytes;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+            __syncwarp();  // the entry-by-entry copies before lane 0's arrive (release)
+            if (lane == 0) mbar_expect_tx(bar, total);
+        }
+        __syncwarp();  // the expected bytes raised before any run's copy can complete
+        if (bytes) {
+            fence_proxy_async();
+            bulk_g2s(smem_u32(wdst + (size_t)pos * wn.xsize), (const char *)wn.x + (size_t)c0 * wn.xsize, bytes, bar);
+        }
     };
     if (threadIdx.x == 0) {
         for (int st = 0; st < S; ++st) {
@@ -209,13 +334,24 @@ __device__ __forceinline__ bool staged_tiles_gated(const Sell &A, const TA *__re
         fence_proxy_async_all();  // the basis rows an earlier kernel wrote, before the first bulk copy
         int k = 0;
         const int pre = min(S, max(0, tile_end - tile_begin));
+        prefetch(tile_begin);
         for (; k < pre; ++k) {
-            issue(tile_begin + k, k);
+            issue(tile_begin + k, k, !WIN);
             __syncwarp();
         }
         if (!gate()) {
+            if constexpr (WIN)  // complete the phases the matrix copies were issued under
+                if (lane == 0)
+                    for (int kk = 0; kk < pre; ++kk) mbar_arrive(smem_u32(full + kk));
             for (int kk = 0; kk < pre; ++kk) mbar_wait(smem_u32(full + kk), 0u);
             return false;
+        }
+        if constexpr (WIN) {
+            fence_proxy_async_all();  // x, written by the grid the gate waited for, before its bulk copies
+            for (int kk = 0; kk < pre; ++kk) {
+                issue_window(kk);
+                __syncwarp();
+            }
         }
         for (int t = tile_begin + k; t < tile_end; ++t, ++k) {
             const int st = k % S;
@@ -223,8 +359,12 @@ __device__ __forceinline__ bool staged_tiles_gated(const Sell &A, const TA *__re
                 ok = false;
                 break;
             }
-            issue(t, st);
+            issue(t, st, !WIN);
             __syncwarp();
+            if constexpr (WIN) {
+                issue_window(st);
+                __syncwarp();
+            }
         }
         // wait for the copies of the last (up to S) tiles issued, so none lands after exit
         const int issued = k;
@@ -252,8 +392,12 @@ __device__ __forceinline__ bool staged_tiles_gated(const Sell &A, const TA *__re
                 StageView<TA> v;
                 v.w = (b1 - b0) >> 5;
                 v.col = reinterpret_cast<const int *>(body_base) + (b0 - bt);
-                v.val = reinterpret_cast<const TA *>(body_base + (size_t)tile_nnz * 4) + (b0 - bt);
-                v.extra = body_base + (size_t)tile_nnz * (4 + sizeof(TA));
+                v.lcol = reinterpret_cast<const uint16_t *>(body_base) + (b0 - bt);
+                v.val = reinterpret_cast<const TA *>(body_base + (size_t)tile_nnz * kIdxBytes) + (b0 - bt);
+                v.extra = body_base + (size_t)tile_nnz * (kIdxBytes + sizeof(TA));
+                v.win = v.extra + (size_t)ex.count * kTileRows * ex.esize;
+                if constexpr (WIN) v.own = reinterpret_cast<const int *>(base + kStageOffs)[kWinRecOwn];
+                else v.own = 0;
                 v.esize = ex.esize;
                 v.row0 = warp * kSlice;
                 body(s, v);
@@ -266,17 +410,23 @@ __device__ __forceinline__ bool staged_tiles_gated(const Sell &A, const TA *__re
 }
 
 // staged_tiles_gated without a gate (the caller waited already)
-template <class TA, int S, bool EVICT_FIRST = false, class Body>
+template <class TA, int S, bool EVICT_FIRST = false, bool WIN = false, class Body>
 __device__ __forceinline__ bool staged_tiles(const Sell &A, const TA *__restrict__ val, int tile_begin,
                                              int tile_end, char *ring, int stage_bytes, uint64_t *full,
-                                             uint64_t *empty, Extra ex, int *err, Body body) {
-    return staged_tiles_gated<TA, S, EVICT_FIRST>(A, val, tile_begin, tile_end, ring, stage_bytes, full, empty, ex,
-                                                  err, body, [] { return true; });
+                                             uint64_t *empty, Extra ex, int *err, Body body,
+                                             Window wn = Window()) {
+    return staged_tiles_gated<TA, S, EVICT_FIRST, WIN>(A, val, tile_begin, tile_end, ring, stage_bytes, full, empty,
+                                                       ex, err, body, [] { return true; }, wn);
 }
 
-// stage size in bytes for tiles of slices up to wmax wide
-__host__ __device__ inline int stage_bytes_for(int wmax, int asize, int n_extra, int esize) {
-    const int b = kStageHdr + kTileSlices * wmax * kSlice * (4 + asize) + n_extra * kTileRows * esize;
+// stage size in bytes for tiles of slices up to wmax wide; win_entries > 0:
+// windowed tiles (2-byte indices) with x windows of up to that many entries
+// of xsize bytes
+__host__ __device__ inline int stage_bytes_for(int wmax, int asize, int n_extra, int esize, int win_entries = 0,
+                                               int xsize = 0) {
+    const int isz = win_entries > 0 ? 2 : 4;
+    const int b = kStageHdr + kTileSlices * wmax * kSlice * (isz + asize) + n_extra * kTileRows * esize +
+                  (win_entries > 0 ? win_entries * xsize + kWinPadBytes : 0);
     return (b + 15) / 16 * 16;
 }
 

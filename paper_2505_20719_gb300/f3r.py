@@ -83,6 +83,8 @@ def lib():
         L.f3r_get_rich_state.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64)]
         L.f3r_set_rich_state.argtypes = [vp, C.POINTER(C.c_double), C.c_int64]
         L.f3r_export.argtypes = [vp, C.c_int, vp]
+        L.f3r_matrix_info.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.f3r_matrix_info.restype = C.c_int
         L.f3r_device_bytes.argtypes = [vp]
         L.f3r_device_bytes.restype = C.c_int64
         L.f3r_destroy.argtypes = [vp]
@@ -299,7 +301,8 @@ class Solver:
     def export(self, which: int, nnz: int = None) -> np.ndarray:
         """Set-up arrays in CSR order: 0 d, 1 A^ f64, 2 A^ f32, 3 A^/s f16 bits,
         4 A^/s bf16 bits, 5 row scales, 6 M (m_prec); approximate inverse:
-        7 L Dt^-1, 8 Dt^-1 U (f16 bits, nnz), 9 Dt^-1 (f16 bits, n)."""
+        7 L Dt^-1, 8 Dt^-1 U (f16 bits, nnz), 9 Dt^-1 (f16 bits, n); 10 the
+        column each windowed entry stands for (int32, nnz)."""
         n = self.n
         if which == 0:
             out = np.empty(n, np.float64)
@@ -311,6 +314,8 @@ class Solver:
             out = np.empty(nnz, np.uint16)
         elif which == 9:
             out = np.empty(n, np.uint16)
+        elif which == 10:
+            out = np.empty(nnz, np.int32)
         elif which == 5:
             out = np.empty(n, np.float32)
         else:
@@ -370,6 +375,13 @@ class Solver:
     @property
     def device_bytes(self) -> int:
         return lib().f3r_device_bytes(self.h)
+
+    def matrix_info(self) -> dict:
+        """Storage of the set-up matrix (f3r_matrix_info)."""
+        out = (C.c_int64 * 8)()
+        _check(lib().f3r_matrix_info(self.h, out), "f3r_matrix_info")
+        keys = ("windowed", "win_max", "nsell", "wmax", "nslices", "index_bytes", "win_chunk", "m_unit")
+        return {k: int(v) for k, v in zip(keys, out)}
 
 
 class BatchedSolver:
