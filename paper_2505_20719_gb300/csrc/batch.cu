@@ -810,7 +810,7 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
         c->prm = prm;
         c->n = d.n;
         c->nnz = d.nnz;
-        c->ld = (int)(((long long)d.n + 255) / 256 * 256);
+        c->ld = (int)(((long long)d.n + kTileRows - 1) / kTileRows * kTileRows);  // whole tiles
         if (d.n >= split) {
             const f3r_status st = f3r_setup(&b->full[k], d.n, d.nnz, d.rowptr, d.colidx, d.val, &prm, (void *)s);
             if (st != F3R_OK) return fail(st);

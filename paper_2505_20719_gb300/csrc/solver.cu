@@ -354,7 +354,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     c.prm = prm;
     c.n = n;
     c.nnz = nnz;
-    c.ld = (int)(((long long)n + 255) / 256 * 256);  // whole 256-row tiles
+    c.ld = (int)(((long long)n + kTileRows - 1) / kTileRows * kTileRows);  // whole tiles
     if (cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) != cudaSuccess) {
         delete h;
         return F3R_ERR_CUDA;

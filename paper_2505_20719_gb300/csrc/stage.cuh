@@ -121,8 +121,13 @@ struct Extra {
     int esize = 4;
 };
 
-constexpr int kTileSlices = kWarps;              // one slice per warp of the block
-constexpr int kTileRows = kTileSlices * kSlice;  // 256 rows per tile
+// A tile is kTileSlices slices; consumer warp w takes slices w, w + kWarps, ...
+#ifndef F3R_TILE_SLICES
+#define F3R_TILE_SLICES 16
+#endif
+constexpr int kTileSlices = F3R_TILE_SLICES;
+constexpr int kTileRows = kTileSlices * kSlice;  // 512 rows per tile
+static_assert(kTileSlices % kWarps == 0 && kTileSlices < 32, "whole slices per consumer warp, offsets in one warp");
 
 // Windowed tiles.  The columns the rows of one tile reference, and the
 // tile's own rows, are covered by at most kWinRuns runs of consecutive x
@@ -381,26 +386,29 @@ __device__ __forceinline__ bool staged_tiles_gated(const Sell &A, const TA *__re
                 if (lane == 0) atomicOr(err, ERR_STAGE_TIMEOUT);
                 break;
             }
-            const int s = t * kTileSlices + warp;
-            if (s < A.nslices) {
-                const char *base = ring + (size_t)st * stage_bytes;
-                const int *hdr = reinterpret_cast<const int *>(base);
-                const int bt = hdr[0];
-                const int tile_nnz = hdr[kTileSlices] - bt;
-                const int b0 = hdr[warp], b1 = hdr[warp + 1];
-                const char *body_base = base + kStageHdr;
-                StageView<TA> v;
-                v.w = (b1 - b0) >> 5;
-                v.col = reinterpret_cast<const int *>(body_base) + (b0 - bt);
-                v.lcol = reinterpret_cast<const uint16_t *>(body_base) + (b0 - bt);
-                v.val = reinterpret_cast<const TA *>(body_base + (size_t)tile_nnz * kIdxBytes) + (b0 - bt);
-                v.extra = body_base + (size_t)tile_nnz * (kIdxBytes + sizeof(TA));
-                v.win = v.extra + (size_t)ex.count * kTileRows * ex.esize;
-                if constexpr (WIN) v.own = reinterpret_cast<const int *>(base + kStageOffs)[kWinRecOwn];
-                else v.own = 0;
-                v.esize = ex.esize;
-                v.row0 = warp * kSlice;
-                body(s, v);
+            const char *base = ring + (size_t)st * stage_bytes;
+            const int *hdr = reinterpret_cast<const int *>(base);
+            const int bt = hdr[0];
+            const int tile_nnz = hdr[kTileSlices] - bt;
+            const char *body_base = base + kStageHdr;
+            StageView<TA> v;
+            v.extra = body_base + (size_t)tile_nnz * (kIdxBytes + sizeof(TA));
+            v.win = v.extra + (size_t)ex.count * kTileRows * ex.esize;
+            if constexpr (WIN) v.own = reinterpret_cast<const int *>(base + kStageOffs)[kWinRecOwn];
+            else v.own = 0;
+            v.esize = ex.esize;
+#pragma unroll
+            for (int sl = warp; sl < kTileSlices; sl += kWarps) {
+                const int s = t * kTileSlices + sl;
+                if (s < A.nslices) {
+                    const int b0 = hdr[sl], b1 = hdr[sl + 1];
+                    v.w = (b1 - b0) >> 5;
+                    v.col = reinterpret_cast<const int *>(body_base) + (b0 - bt);
+                    v.lcol = reinterpret_cast<const uint16_t *>(body_base) + (b0 - bt);
+                    v.val = reinterpret_cast<const TA *>(body_base + (size_t)tile_nnz * kIdxBytes) + (b0 - bt);
+                    v.row0 = sl * kSlice;
+                    body(s, v);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(empty + st));
