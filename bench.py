@@ -602,6 +602,18 @@ def main():
         # read back, V[0..j] once (avg 2.5), V[j+1] and the next v written
         "f3_step_L2": 2 * (isz + asz) * nnz + 2 * rsb + vsz * n + msz * n + 4 * n + 4 * n + 4 * n * 2.5 + 4 * n + vsz * n,
     }
+    # the same launches' bytes in the stored format: windowed matrices keep a
+    # 2-byte index per stored entry (padding included) instead of the int32
+    # column of the model above; the x window adds the tile's reads of x,
+    # which the model already counts once per row
+    info = s.matrix_info()
+    ns, ib = info["nsell"], info["index_bytes"]
+    stored = {
+        "rich_fused2_L0": (ib + asz) * ns + rsb + vsz * n + msz * n + 4 * n,
+        "spmv_dots_L2": (ib + asz) * ns + rsb + 4 * n + 4 * n + 4 * n * 2.5,
+        "spmv_dots_L1": (ib + 4) * ns + 4 * n + 4 * n + 4 * n * 4.5,
+        "f3_step_L2": 2 * (ib + asz) * ns + 2 * rsb + vsz * n + msz * n + 4 * n + 4 * n + 4 * n * 2.5 + 4 * n + vsz * n,
+    }
     ranked = sorted(prof, key=lambda k: -prof[k]["ms"])
     dk = next((k for k in ranked if k in algo), None)
     avg_s = prof[dk]["avg_us"] * 1e-6
@@ -609,7 +621,14 @@ def main():
     roofline = {"bound": "hbm", "kernel": dk, "achieved": achieved, "peak": hbm, "unit": "GB/s",
                 "frac": achieved / hbm, "peak_source": f"{peak_src} (copy bandwidth, burst)",
                 "algorithmic_bytes_per_launch": algo[dk], "avg_launch_us": prof[dk]["avg_us"],
-                "traffic": _ncu_traffic(dk)}
+                "traffic": _ncu_traffic(dk),
+                "byte_model": "int32 column + value per nonzero (6 bytes fp16), vectors once",
+                "stored_bytes_per_launch": stored[dk],
+                "frac_stored": stored[dk] / avg_s / 1e9 / hbm,
+                "stored_format": ("windowed SELL-32, 2-byte window indices, 512-row tiles" if info["windowed"]
+                                  else "SELL-32, int32 columns"),
+                "time_source": "CUDA events around each launch of one profiled solve (launches not "
+                               "overlapped, so each time includes its launch gap)"}
 
     # ---- stand-alone 16-bit SpMV (f3r_spmv), the metric's second half
     sp_prec = {"fp16-F3R": f3r.F16, "bf16-F3R": f3r.BF16, "fp32-F3R": f3r.F32}.get(args.kind, f3r.F64)
@@ -618,6 +637,7 @@ def main():
     for _ in range(5):
         s.spmv(sp_prec, f3r.F32, xs, ys, stream=stream)
     sp_bytes = (isz + asz) * nnz + rsb + 4 * n + 4 * n
+    sp_stored = (ib + asz) * ns + rsb + 4 * n + 4 * n
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     cold = []
     for _ in range(20):  # cold: L2 flushed (256 MiB write) before each launch, one launch per event pair
@@ -643,6 +663,8 @@ def main():
             "back_to_back_note": f"{reps} launches on the same x and y after one flush: the working set "
                                  "fits in L2, so later launches read from it"}
     spmv["frac"] = spmv["achieved"] / hbm
+    spmv["stored_bytes_per_launch"] = sp_stored
+    spmv["frac_stored"] = sp_stored / (sp_us * 1e-6) / 1e9 / hbm
 
     # ---- per-level error of the low-precision levels against the fp64 path (same inputs)
     level_errors = level_error_report(prob, rp, ci, va, ds, dev, stream)

@@ -337,7 +337,9 @@ void f3r_destroy_batched(f3r_batch *batch);
  *     rows); larger n, n <= 0 or a NULL pointer return F3R_ERR_ARG.
  *   - The first call on a device looks up that device's address of the
  *     scratch array (with the device current); make that first call before
- *     any stream capture.
+ *     any stream capture.  The address is kept per device and CUDA context:
+ *     after a cudaDeviceReset the next call looks it up again in the new
+ *     context (again before any capture).
  *   - All calls share the one scratch array, which keeps the last call's
  *     contents (each call clears the part that must start at zero), so calls
  *     that overlap on the GPU -- on different streams or host threads -- race

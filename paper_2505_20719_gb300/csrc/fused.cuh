@@ -21,7 +21,10 @@
 
 namespace f3r {
 
-constexpr int kFusedThreads = 512;
+#ifndef F3R_FUSED_THREADS
+#define F3R_FUSED_THREADS 512
+#endif
+constexpr int kFusedThreads = F3R_FUSED_THREADS;
 constexpr int kFusedWarps = kFusedThreads / 32;
 constexpr int kFusedChunkAlign = 64;  // rows; keeps every chunk 256-byte aligned
 enum { ERR_BARRIER_TIMEOUT = 2 };
@@ -131,7 +134,7 @@ __device__ __forceinline__ T warp_sum_partials(const T *p, int G, int stride, bo
 }
 
 template <class T, class TC, int CHILD, int MAXD>
-__global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8) ? 2 : 1)
+__global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8 && kFusedThreads <= 512) ? 2 : 1)
     k_cgs_fused(LevelDev<T> L, int j, int passes, int last_iter, int want_sigma, int do_norm, ChildOut<TC> co,
                 FusedScratch<T> fs, GridRed<TC> grc) {
     if (stopped(L.flags, L.depth)) return;  // the same answer in every block: no barrier is entered
@@ -363,7 +366,7 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8) ? 2 : 1)
 constexpr int kOuterGroup = 8;
 
 template <class TC, int CHILD>
-__global__ void __launch_bounds__(kFusedThreads, 2)
+__global__ void __launch_bounds__(kFusedThreads, kFusedThreads <= 512 ? 2 : 1)
     k_outer_cgs_fused(LevelDev<double> L, int passes, ChildOut<TC> co, FusedScratch<double> fs, GridRed<TC> grc) {
     constexpr int N = 2;  // double2 packs
     extern __shared__ __align__(16) unsigned char fused_dsm[];

@@ -6,6 +6,8 @@
 // scratch (one pair of partial sums per block and the ticket that elects the
 // block finishing the reduction) lives in the file-scope array below, which
 // every GPU that loads this library keeps until the process exits.
+#include <cuda.h>  // CUcontext and the driver call's signature only; libcuda is reached through the runtime
+
 #include <mutex>
 
 #include "common.cuh"
@@ -95,7 +97,9 @@ __global__ void __launch_bounds__(kNaBlock) k_residual_noalloc(int n, const int 
 }
 
 std::mutex g_na_mutex;
+// per device: the scratch array's address in the context it was looked up in
 unsigned char *g_na_addr[kNaMaxDevices] = {};
+CUcontext g_na_ctx[kNaMaxDevices] = {};
 
 }  // namespace
 
@@ -113,15 +117,35 @@ extern "C" f3r_status f3r_residual_noalloc(int32_t n, const int32_t *rowptr, con
     unsigned char *scratch = nullptr;
     {
         // The array's name is only a host-side stand-in; its device address is
-        // looked up once per device, with that device current.
+        // looked up once per device and context, with that device current (a
+        // cudaDeviceReset ends the context, and the next call looks it up in
+        // the new one).
         std::lock_guard<std::mutex> lock(g_na_mutex);
-        if (!g_na_addr[dev]) {
+        static CUresult (*ctx_current)(CUcontext *) = nullptr;
+        if (!ctx_current) {
+            cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+            void *fn = nullptr;
+            if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess ||
+                q != cudaDriverEntryPointSuccess || !fn) {
+                cudaGetLastError();
+                return F3R_ERR_CUDA;
+            }
+            ctx_current = reinterpret_cast<CUresult (*)(CUcontext *)>(fn);
+        }
+        CUcontext ctx = nullptr;
+        if (cudaFree(nullptr) != cudaSuccess || ctx_current(&ctx) != CUDA_SUCCESS || !ctx) {
+            cudaGetLastError();
+            return F3R_ERR_CUDA;
+        }
+        if (!g_na_addr[dev] || g_na_ctx[dev] != ctx) {
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_na_scratch) != cudaSuccess || !p) {
                 cudaGetLastError();
                 return F3R_ERR_CUDA;
             }
             g_na_addr[dev] = (unsigned char *)p;
+            g_na_ctx[dev] = ctx;
         }
         scratch = g_na_addr[dev];
     }

@@ -56,6 +56,43 @@ def test_residual_noalloc_matches_existing_entry_points():
     s.close()
 
 
+def _tridiagonal(n, seed):
+    """1-D Laplacian-like CSR matrix (3 entries per row), fp64."""
+    rng = np.random.default_rng(seed)
+    rows = np.arange(n)
+    cols = np.stack([rows - 1, rows, rows + 1], axis=1)
+    vals = np.stack([-np.ones(n), 2.0 + rng.random(n), -np.ones(n)], axis=1)
+    keep = (cols >= 0) & (cols < n)
+    rowptr = np.zeros(n + 1, dtype=np.int32)
+    rowptr[1:] = np.cumsum(keep.sum(axis=1))
+    return rowptr, cols[keep].astype(np.int32), vals[keep], rng.random(n), rng.standard_normal(n)
+
+
+@pytest.mark.parametrize("n", [700, 4 * 1024 * 1024 - 4])
+def test_residual_noalloc_single_block_and_full_scratch(n):
+    """One block (n < 1024 rows) and the largest grid the scratch holds (4096
+    blocks, so the last block sums 4096 partials): the residual equals
+    b - f3r_spmv(A, x) bit for bit and the norms match, on two calls in a row."""
+    rowptr, colidx, val, b_h, x_h = _tridiagonal(n, seed=302 + n % 7)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    rp, ci, va, b = d(rowptr), d(colidx), d(val), d(b_h)
+    s = f3r.Solver(rp, ci, va, f3r.default_params(diag_scale=0))
+    lib = f3r.lib()
+    for call in range(2):
+        x = d(x_h * (1.0 + call))
+        r = torch.full((n,), np.nan, dtype=torch.float64, device="cuda")
+        norms = torch.full((2,), np.nan, dtype=torch.float64, device="cuda")
+        assert lib.f3r_residual_noalloc(n, _p(rp), _p(ci), _p(va), _p(b), _p(x), _p(r), _p(norms), None) == f3r.OK
+        y = torch.empty(n, dtype=torch.float64, device="cuda")
+        s.spmv(f3r.F64, f3r.F64, x, y)
+        torch.cuda.synchronize()
+        assert torch.equal(r, b - y)
+        nr, nb = norms.cpu().numpy()
+        assert nb == pytest.approx(np.linalg.norm(b_h), rel=1e-12)
+        assert nr == pytest.approx(float(torch.linalg.norm(b - y)), rel=1e-12)
+    s.close()
+
+
 def test_residual_noalloc_rejects_sizes_beyond_its_scratch():
     lib = f3r.lib()
     dummy = torch.zeros(4, dtype=torch.float64, device="cuda")
