@@ -296,8 +296,8 @@ def run_batched(args):
 def run_learned(args):
     """Learned preconditioner (a 3-layer message-passing net) against Jacobi as
     the M of the fp16 Richardson level: train on 100^3 with pairs (r, A^-1 r)
-    from the fp64 solver (r seeded normal vectors), then time fp16-F3R to 1e-9
-    on 160^3 with each M."""
+    built from the fp64 solver's own Arnoldi vectors, then time fp16-F3R to
+    1e-9 on 160^3 with each M."""
     import torch
     from paper_2505_20719_gb300 import f3r
     from problems import generators as G
@@ -308,21 +308,13 @@ def run_learned(args):
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     tr = G.diffusion27_nodal(100)
     n = tr.n
-    s64 = f3r.Solver(T(tr.rowptr), T(tr.colidx), T(tr.val), f3r.preset("fp64-F3R", tol=1e-10))
-    d = s64.export(0)  # D^-1/2: A^ e = r  <=>  A (D^-1/2 e) = D^1/2 r
+    # (residual, correction) pairs from the fp64 solver's own Arnoldi vectors on
+    # the training system, corrections by fp64 solves to 1e-10
     npairs = 16
-    R = torch.empty(npairs, n, dtype=torch.float32, device=dev)
-    E = torch.empty(npairs, n, dtype=torch.float32, device=dev)
     t0 = time.perf_counter()
-    for k in range(npairs):
-        r = rng.normal(900 + k, 7, n)
-        x = torch.zeros(n, dtype=torch.float64, device=dev)
-        s64.solve(T(r / d), x)
-        R[k] = T(r).float()
-        E[k] = (x / T(d)).float()
+    R, E = f3r.arnoldi_training_pairs(T(tr.rowptr), T(tr.colidx), T(tr.val), T(tr.b), npairs, tol=1e-10)
     torch.cuda.synchronize()
     t_pairs = time.perf_counter() - t0
-    s64.close()
     st = f3r.Solver(T(tr.rowptr), T(tr.colidx), T(tr.val), f3r.default_params(precond=f3r.PC_LEARNED))
     st.learned_load(LI.flatten(LI.init_params(readout_scale=0.0)).astype(np.float32), train=True)
     kind = {"error": 0, "residual": 1}[args.learned_loss]
@@ -378,7 +370,8 @@ def run_learned(args):
            "value": out["learned"]["ms"], "unit": "ms", "n_gpus": 1, "steps": args.steps, "warmup": 1,
            "higher_is_better": False, "data": "synthetic",
            "config": {"workload": "learned27", "desc": WORKLOADS["learned27"], "train_n": n, "eval_n": ev.n,
-                      "eval_nnz": ev.nnz, "pairs": npairs, "train_steps": steps, "batch": 4, "lr": 2e-3,
+                      "eval_nnz": ev.nnz, "pairs": npairs, "pair_source": "Arnoldi vectors of the fp64 solver",
+                      "train_steps": steps, "batch": 4, "lr": 2e-3,
                       "loss": args.learned_loss},
            "learned": out["learned"], "jacobi": out["jacobi"],
            "speedup_vs_jacobi": out["jacobi"]["ms"] / out["learned"]["ms"],
@@ -496,6 +489,8 @@ def main():
     ap.add_argument("--kind", default="fp16-F3R")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--comparators", default="fp32-F3R,fp64-F3R,fgmres64,cg,bicgstab",
+                    help="comma-separated comparators solved on the same GPU")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--fuse-cgs", type=int, default=1, choices=[0, 1],
                     help="1: CGS2 + normalisation of each inner iteration in one cooperative launch")
@@ -671,8 +666,9 @@ def main():
 
     # ---- comparators on the same GPU (one solve each)
     comparators = {}
+    wanted = [c for c in args.comparators.split(",") if c]
     if not args.no_comparators:
-        for kind in ("fp32-F3R", "fp64-F3R", "fgmres64"):
+        for kind in [k for k in ("fp32-F3R", "fp64-F3R", "fgmres64") if k in wanted]:
             cp = f3r.preset(kind, diag_scale=ds)
             sc = f3r.Solver(rp, ci, va, cp, stream=stream)
             xc = torch.zeros(n, dtype=torch.float64, device=dev)
@@ -688,7 +684,7 @@ def main():
             sc.close()
             del xc
         # the paper's CG / BiCGStab comparators (fp64, same preconditioner)
-        for method in ("cg", "bicgstab"):
+        for method in [m for m in ("cg", "bicgstab") if m in wanted]:
             xc = torch.zeros(n, dtype=torch.float64, device=dev)
             s.solve_krylov(method, b, xc, stream=stream)  # warm-up (graph capture)
             xc.zero_()
@@ -704,6 +700,8 @@ def main():
         # comparator that stopped without reaching it
         for key, kind in (("fgmres64", "fgmres64"), ("fp64_f3r", "fp64-F3R"), ("fp32_f3r", "fp32-F3R"),
                           ("cg", "cg"), ("bicgstab", "bicgstab")):
+            if kind not in comparators:
+                continue
             c = comparators[kind]
             conv = c["status"] == f3r.STATUS[f3r.OK]
             comparators[f"speedup_vs_{key}"] = c["ms"] / ms_per_solve if conv else None

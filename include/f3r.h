@@ -162,6 +162,14 @@ f3r_status f3r_spmv(f3r_ctx *ctx, int p, int vp, const void *x, void *y, void *s
  * x and z are device pointers of n elements. */
 f3r_status f3r_apply(f3r_ctx *ctx, int level, const void *x, void *z, void *stream);
 
+/* Copy basis vector V[k] (0 <= k <= m of that level) of FGMRES level `level`
+ * as the context's last call left it -- for level 0 the last restart cycle of
+ * the last f3r_solve: the normalised residual (k = 0) and the Arnoldi vectors
+ * of the outer fp64 FGMRES (Sec. 4.2) -- into `out` (n elements in the
+ * level's vector precision; host or device memory).  Used to build training
+ * pairs for the learned preconditioner from the solver's own vectors. */
+f3r_status f3r_get_basis(f3r_ctx *ctx, int level, int k, void *out, void *stream);
+
 /* Read / write the Richardson state (omega[0..m4-1], call counter c_ntr). */
 f3r_status f3r_get_rich_state(f3r_ctx *ctx, double *omega8, int64_t *c_ntr);
 f3r_status f3r_set_rich_state(f3r_ctx *ctx, const double *omega8, int64_t c_ntr);

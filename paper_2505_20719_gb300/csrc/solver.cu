@@ -674,6 +674,24 @@ f3r_status f3r_apply(f3r_ctx *h, int level, const void *x, void *z, void *stream
     return cudaGetLastError() == cudaSuccess ? F3R_OK : F3R_ERR_CUDA;
 }
 
+f3r_status f3r_get_basis(f3r_ctx *h, int level, int k, void *out, void *stream) {
+    if (!h || !out) return F3R_ERR_ARG;
+    Ctx &c = h->c;
+    if (level < 0 || level >= c.prm.nlevels || k < 0 || k > c.L[level].m) return F3R_ERR_ARG;
+    const size_t eb = (size_t)prec_bytes(c.L[level].v_prec);
+    const char *src = (const char *)c.L[level].V + (size_t)k * c.ld * eb;
+    cudaStream_t s = (cudaStream_t)stream;
+    // ordered after the context's own work (the solve that left the basis)
+    cudaEventRecord(c.ev1, h->cs);
+    cudaStreamWaitEvent(s, c.ev1, 0);
+    if (cudaMemcpyAsync(out, src, eb * (size_t)c.n, cudaMemcpyDefault, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return F3R_ERR_CUDA;
+    }
+    return F3R_OK;
+}
+
 f3r_status f3r_get_rich_state(f3r_ctx *h, double *omega8, int64_t *c_ntr) {
     if (!h) return F3R_ERR_ARG;
     if (omega8)

@@ -132,11 +132,12 @@ __global__ void __launch_bounds__(kStagedThreads) k_spmv_dots_st(Sell A, const T
     wn.x = x;
     staged_tiles_gated<TA, S, true, WIN>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), ex, cfg.err,
                         [&](int s, const StageView<TA> &v) {
+                             const int i = s * kSlice + lane;
+                             const T rsi = rs ? (T)__ldg(rs + i) : (T)1;  // requested before the row sum
                              T y;
                              if constexpr (WIN) y = staged_row<T, true>(v, lane, [&](int c) { return v.template xwin<T>()[c]; });
                              else y = staged_row<T>(v, lane, [&](int c) { return __ldg(x + c); });
-                             const int i = s * kSlice + lane;
-                             if (rs) y = mul_rn(y, (T)__ldg(rs + i));
+                             if (rs) y = mul_rn(y, rsi);
                              if (i < L.n) {
                                  L.w[i] = y;
 #pragma unroll
@@ -181,6 +182,8 @@ __global__ void __launch_bounds__(kStagedThreads) k_rich2_st(Sell A, const TA *_
     wn.x = v;
     staged_tiles_gated<TA, S, false, WIN>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), Extra(), cfg.err,
                         [&](int s, const StageView<TA> &st) {
+                             const int i = s * kSlice + lane;
+                             const TC rsi = rs ? (TC)__ldg(rs + i) : (TC)1;  // requested before the row sum
                              TC acc;
                              if constexpr (WIN) {
                                  const VS *xw = st.template xwin<VS>();
@@ -193,8 +196,7 @@ __global__ void __launch_bounds__(kStagedThreads) k_rich2_st(Sell A, const TA *_
                                      return rnd<VS>(fma_rn(w1, UNIT ? vc : mul_rn(to_c<TC>(__ldg(mv + c)), vc), (TC)0));
                                  });
                              }
-                             const int i = s * kSlice + lane;
-                             if (rs) acc = mul_rn(acc, (TC)__ldg(rs + i));
+                             if (rs) acc = mul_rn(acc, rsi);
                              if (i < n) {
                                  TC vi;  // the row's own v: from the window (it holds the tile's rows)
                                  if constexpr (WIN) vi = to_c<TC>(st.template xwin<VS>()[st.own + st.row0 + lane]);
@@ -234,11 +236,12 @@ __global__ void __launch_bounds__(kStagedThreads) k_spmv_st(Sell A, const TA *__
     wn.x = x;
     staged_tiles<TA, S, false, WIN>(A, val, tr.x, tr.y, block_ring(dsm), cfg.stage_bytes, block_full(dsm), block_empty(dsm), Extra(), cfg.err,
                         [&](int s, const StageView<TA> &st) {
+                             const int i = s * kSlice + lane;
+                             const TY rsi = rs ? (TY)__ldg(rs + i) : (TY)1;  // requested before the row sum
                              TY acc;
                              if constexpr (WIN) acc = staged_row<TY, true>(st, lane, [&](int c) { return to_c<TY>(st.template xwin<TX>()[c]); });
                              else acc = staged_row<TY>(st, lane, [&](int c) { return to_c<TY>(__ldg(x + c)); });
-                             const int i = s * kSlice + lane;
-                             if (rs) acc = mul_rn(acc, (TY)__ldg(rs + i));
+                             if (rs) acc = mul_rn(acc, rsi);
                              if (i < A.n) y[i] = acc;
                          }, wn);
 }

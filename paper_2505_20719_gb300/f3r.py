@@ -85,6 +85,7 @@ def lib():
         L.f3r_export.argtypes = [vp, C.c_int, vp]
         L.f3r_matrix_info.argtypes = [vp, C.POINTER(C.c_int64)]
         L.f3r_matrix_info.restype = C.c_int
+        L.f3r_get_basis.argtypes = [vp, C.c_int, C.c_int, vp, vp]
         L.f3r_device_bytes.argtypes = [vp]
         L.f3r_device_bytes.restype = C.c_int64
         L.f3r_destroy.argtypes = [vp]
@@ -288,6 +289,11 @@ class Solver:
     def apply(self, level: int, x, z, stream=None):
         _check(lib().f3r_apply(self.h, level, _ptr(x), _ptr(z), _stream(stream)), "f3r_apply")
 
+    def get_basis(self, level: int, k: int, out, stream=None):
+        """V[k] of FGMRES level `level` after the last call (f3r_get_basis) into `out`."""
+        _check(lib().f3r_get_basis(self.h, level, k, _ptr(out), _stream(stream)), "f3r_get_basis")
+        return out
+
     def rich_state(self):
         om = (C.c_double * 8)()
         cn = C.c_int64()
@@ -442,3 +448,35 @@ class BatchedSolver:
             self.close()
         except Exception:
             pass
+
+
+def arnoldi_training_pairs(rowptr, colidx, val, b, npairs: int, tol: float = 1e-10, stream=None):
+    """Training pairs (r, e) for the learned preconditioner from the fp64
+    solver's own vectors: the Arnoldi vectors v_0..v_{npairs-1} of one cycle
+    of the outer fp64 FGMRES on A x = b (all levels fp64), mapped into the
+    scaled system the Richardson level works in, r = D^-1/2 v, with e =
+    A^^-1 r = D^1/2 A^-1 v from fp64 solves to `tol`.  Inputs are CUDA tensors
+    (the CSR arrays and b); returns two (npairs, n) float32 CUDA tensors."""
+    import torch
+
+    n = len(rowptr) - 1
+    dev = b.device
+    rec = Solver(rowptr, colidx, val, preset("fp64-F3R", tol=1e-300, max_outer=npairs,
+                                             m=[max(npairs, 1), 8, 4, 0]), stream=stream)
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    rec.solve(b, x, stream=stream)  # npairs outer iterations, one cycle: V[0..npairs] kept
+    d = torch.from_numpy(rec.export(0)).to(dev)  # D^-1/2
+    V = torch.empty(npairs, n, dtype=torch.float64, device=dev)
+    for k in range(npairs):
+        rec.get_basis(0, k, V[k], stream=stream)
+    rec.close()
+    sol = Solver(rowptr, colidx, val, preset("fp64-F3R", tol=tol), stream=stream)
+    R = torch.empty(npairs, n, dtype=torch.float32, device=dev)
+    E = torch.empty(npairs, n, dtype=torch.float32, device=dev)
+    for k in range(npairs):
+        x.zero_()
+        sol.solve(V[k], x, stream=stream)  # A x = v_k
+        R[k] = (d * V[k]).float()
+        E[k] = (x / d).float()
+    sol.close()
+    return R, E

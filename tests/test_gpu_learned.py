@@ -105,21 +105,31 @@ def test_residual_loss_gradient_matches_oracle(setup):
         assert np.linalg.norm(a - b) <= 2e-2 * np.linalg.norm(b) + 1e-6, k
 
 
+def test_arnoldi_training_pairs(setup):
+    """Pairs from the fp64 solver's own Arnoldi vectors: r_k = D^-1/2 v_k with
+    v_k orthonormal, and e_k solving A^ e_k = r_k."""
+    prob, s, A16 = setup
+    import scipy.sparse as sp
+    rp, ci, va, b = dev(prob.rowptr), dev(prob.colidx), dev(prob.val), dev(prob.b)
+    R, E = f3r.arnoldi_training_pairs(rp, ci, va, b, 6, tol=1e-11)
+    P = O.Problem(prob, diag_scale=1)
+    d = P.get("d")
+    Ah = sp.csr_matrix((P.get("ahat"), prob.colidx, prob.rowptr), shape=(prob.n, prob.n))
+    Rh, Eh = R.double().cpu().numpy(), E.double().cpu().numpy()
+    Vh = Rh / d  # back to the original space: v_k = D^1/2 r_k
+    G = Vh @ Vh.T
+    assert np.abs(G - np.eye(6)).max() < 1e-5  # orthonormal up to the fp32 storage of r
+    for k in range(6):
+        assert np.linalg.norm(Ah @ Eh[k] - Rh[k]) <= 1e-6 * np.linalg.norm(Rh[k])
+
+
 def test_training_reduces_loss_and_solves(setup):
     prob, s, A16 = setup
     n = prob.n
-    # (residual, correction) pairs from the fp64 solver: A^ e = r in the scaled system
-    s64 = f3r.Solver(dev(prob.rowptr), dev(prob.colidx), dev(prob.val), f3r.preset("fp64-F3R", tol=1e-11))
-    d = s64.export(0)  # D^-1/2
-    R, E = [], []
-    for k in range(8):
-        r = rng.normal(20 + k, 7, n)
-        x = np.zeros(n)
-        s64.solve(np.ascontiguousarray(r / d), x)  # A x = D^1/2 r  <=>  A^ (D^-1/2 x) ... e = x / d
-        R.append(r)
-        E.append(x / d)
-    R = np.array(R, np.float32)
-    E = np.array(E, np.float32)
+    # (residual, correction) pairs from the fp64 solver's Arnoldi vectors
+    R, E = f3r.arnoldi_training_pairs(dev(prob.rowptr), dev(prob.colidx), dev(prob.val), dev(prob.b), 8,
+                                      tol=1e-11)
+    R, E = R.cpu().numpy(), E.cpu().numpy()
     s.learned_load(LI.flatten(LI.init_params(readout_scale=0.0)).astype(np.float32), train=True)
     l0, _ = s.learned_loss_grad(dev(R), dev(E))
     hist = s.learned_train(dev(R), dev(E), steps=150, batch=4, lr=3e-3)
@@ -135,3 +145,41 @@ def test_training_reduces_loss_and_solves(setup):
     rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
     assert res.status == f3r.OK and rel < 1e-9
     assert res.m_applies == 64 * res.outer_iters
+
+
+def test_learned_against_jacobi_reported(setup):
+    """What the trained net gains (or loses) against Jacobi-F3R on the same
+    system and tolerance: outer iterations and solve time of both, printed.
+    Asserted: both reach 1e-9 on the true residual (the fp64 outer level
+    judges), and the net was trained (its training loss fell)."""
+    prob, s, A16 = setup
+    n = prob.n
+    rp, ci, va, b = dev(prob.rowptr), dev(prob.colidx), dev(prob.val), dev(prob.b)
+    R, E = f3r.arnoldi_training_pairs(rp, ci, va, b, 8, tol=1e-11)
+    st = f3r.Solver(rp, ci, va, f3r.default_params(precond=f3r.PC_LEARNED))
+    st.learned_load(LI.flatten(LI.init_params(readout_scale=0.0)).astype(np.float32), train=True)
+    st.learned_set_loss(1)
+    l0, _ = st.learned_loss_grad(R, None)
+    st.learned_train(R, E, steps=200, batch=4, lr=3e-3)
+    l1, _ = st.learned_loss_grad(R, None)
+    theta = st.learned_get()
+    st.close()
+    assert l1 < l0
+    A = prob.to_scipy()
+    out = {}
+    for name, prm in (("jacobi", f3r.default_params()), ("learned", f3r.default_params(precond=f3r.PC_LEARNED))):
+        sv = f3r.Solver(rp, ci, va, prm)
+        if name == "learned":
+            sv.learned_load(theta)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        sv.solve(b, x)  # warm-up
+        x.zero_()
+        r = sv.solve(b, x)
+        rel = np.linalg.norm(prob.b - A @ x.cpu().numpy()) / np.linalg.norm(prob.b)
+        out[name] = (r.outer_iters, r.t_solve_ms, rel, r.status)
+        sv.close()
+    print(f"learned M: {out['learned'][0]} outer iterations, {out['learned'][1]:.2f} ms; "
+          f"Jacobi: {out['jacobi'][0]} outer iterations, {out['jacobi'][1]:.2f} ms; "
+          f"time ratio learned/Jacobi {out['learned'][1] / out['jacobi'][1]:.2f}")
+    for name in out:
+        assert out[name][3] == f3r.OK and out[name][2] < 1e-9, (name, out[name])
