@@ -281,11 +281,25 @@ def run_batched(args):
             q += 1
         s.close()
     ninst = len(Bs)
+    info = bs.info()
+    # time of each path: the persistent launch (one graph; every instance in it
+    # reports the launch's time) and the large systems' instances solved one
+    # after another on the whole GPU
+    launch_ms = next((r.t_solve_ms for r in res if r.path == 0), 0.0)
+    single_ms = sum(r.t_solve_ms for r in res if r.path == 1)
     out = {"metric": "batched F3R throughput (systems x right-hand sides solved to 1e-9 per second)",
            "value": ninst / (ms / 1e3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "data": "synthetic",
            "config": {"workload": "batched64", "desc": WORKLOADS["batched64"], "instances": ninst,
-                      "rows_total": int(sum(p.n * B.shape[0] for p, B in batch)), "cluster": chosen},
+                      "rows_total": int(sum(p.n * B.shape[0] for p, B in batch)),
+                      "shape": {"cluster": info["cluster"], "threads_per_block": info["threads"],
+                                "blocks": info["grid"], "chosen_by": "f3r_batched_autotune"}},
+           "paths": {"persistent_launch": {"instances": info["instances_launch"], "rows": info["rows_launch"],
+                                           "ms": launch_ms, "graph_launches": info["graph_launches"]},
+                     "single_system": {"instances": info["instances_single"], "rows": info["rows_single"],
+                                       "ms": single_ms,
+                                       "note": "systems of at least batch_split rows (2048 per SM), solved "
+                                               "one after another on the whole GPU before the launch"}},
            "converged": ok, "max_outer_iters": max(r.outer_iters for r in res),
            "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
            "device_bytes": bs.device_bytes}

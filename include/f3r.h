@@ -298,6 +298,7 @@ typedef struct {
     double t_solve_ms;       /* device time of the whole persistent launch, or of the
                                 instance's own solve (systems of >= batch_split rows) */
     int system, rhs;         /* which instance */
+    int path;                /* 0: the persistent launch; 1: the single-system path */
 } f3r_batch_result;
 
 /* Set up all systems (setup of each matrix as in f3r_setup) and the
@@ -311,21 +312,35 @@ f3r_status f3r_setup_batched(f3r_batch **batch, int nsys, const f3r_system_desc 
 /* Solve every instance: B[q] and X[q] are device pointers (n of system q's
  * system fp64 values) for instance q, instances numbered system by system
  * and right-hand side by right-hand side; X[q] holds x0 on entry.  The
- * instances of large systems first (f3r_solve each), then one kernel launch
- * for the rest; res (optional, one entry per instance) receives each
- * instance's result.  Returns F3R_OK if every instance converged, else the
- * status of the first instance that did not. */
+ * instances of large systems first (f3r_solve each), then one persistent
+ * kernel launch for the rest, replayed as a CUDA graph (the instances' b and x
+ * pointers reach it through a pinned host table that the graph copies to the
+ * device; one graph per cluster and block size, captured on first use, so the
+ * first call should come before any stream capture of the caller's); res
+ * (optional, one entry per instance) receives each instance's result.
+ * Returns F3R_OK if every instance converged, else the status of the first
+ * instance that did not. */
 f3r_status f3r_solve_batched(f3r_batch *batch, const double *const *B, double *const *X, f3r_batch_result *res,
                              void *stream);
 
 /* Thread-block cluster size of the batched launch (1, 2, 4 or 8; default 8). */
 f3r_status f3r_batched_set_cluster(f3r_batch *batch, int cluster_size);
-/* Autotuner: times one outer iteration of the persistent launch's instances (from x0 = 0) for
- * cluster sizes 1, 2, 4 and 8 and keeps the fastest (written to *chosen if
- * not NULL).  B and X as in f3r_solve_batched; X is zero on return. */
+/* Team shape of the batched launch: blocks per instance (the cluster size: 1,
+ * 2, 4 or 8) and threads per block (256 or 512; default 512). */
+f3r_status f3r_batched_set_shape(f3r_batch *batch, int cluster_size, int threads);
+/* Autotuner: times one outer iteration of the persistent launch's instances
+ * (from x0 = 0) for every team shape (cluster sizes 1, 2, 4, 8 times 256 or
+ * 512 threads per block) and keeps the fastest (its cluster size written to
+ * *chosen if not NULL; f3r_batched_info gives both).  B and X as in
+ * f3r_solve_batched; X is zero on return. */
 f3r_status f3r_batched_autotune(f3r_batch *batch, const double *const *B, double *const *X, int *chosen,
                                 void *stream);
 int f3r_batched_instances(const f3r_batch *batch);
+/* How the batch runs, out[8]: [0] cluster size, [1] threads per block, [2]
+ * instances in the persistent launch, [3] instances solved one after another
+ * by the single-system path (systems of >= batch_split rows), [4] / [5] their
+ * rows in all, [6] blocks of the persistent launch, [7] graph launches so far. */
+f3r_status f3r_batched_info(const f3r_batch *batch, int64_t *out);
 int64_t f3r_batched_device_bytes(const f3r_batch *batch);
 void f3r_destroy_batched(f3r_batch *batch);
 

@@ -21,6 +21,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <map>
 #include <vector>
 
 #include "ctx.h"
@@ -31,8 +32,8 @@ namespace cg = cooperative_groups;
 namespace f3r {
 namespace bt {
 
-constexpr int kBT = 512;          // threads per block
-constexpr int kBW = kBT / 32;     // warps per block
+constexpr int kBT = 512;          // threads per block at most (256 or 512, chosen by the autotuner)
+constexpr int kBW = kBT / 32;     // warps per block at most
 constexpr int kMaxCluster = 8;
 constexpr int kRedMax = 16;       // sums per team reduction
 
@@ -129,7 +130,8 @@ __device__ void team_reduce(const Team &tm, Shared &sh, T *acc, int nd, T *out, 
         const int d = threadIdx.x;
         const bool mx = is_max && is_max[d];
         T s = (T)sh.wred[d][0];
-        for (int w = 1; w < kBW; ++w) s = mx ? fmax(s, (T)sh.wred[d][w]) : add_rn(s, (T)sh.wred[d][w]);
+        const int nw = (int)(blockDim.x >> 5);  // 256 or 512 threads per block
+        for (int w = 1; w < nw; ++w) s = mx ? fmax(s, (T)sh.wred[d][w]) : add_rn(s, (T)sh.wred[d][w]);
         sh.red_blk[buf][d] = (double)s;
     }
     team_sync();
@@ -742,9 +744,17 @@ struct f3r_batch {
     bt::Out *d_out = nullptr;
     std::vector<bt::Inst> h_inst;
     std::vector<void *> allocs;
-    int cluster = 8, grid = 0;
+    int cluster = 8, threads = bt::kBT, grid = 0;
     long long bytes = 0;
     cudaStream_t cs = nullptr;
+    // the persistent launch as a CUDA graph per (cluster, threads): the
+    // instance table is copied from pinned memory, the queue reset, the
+    // kernel run and the results copied back to pinned memory
+    bt::Inst *pin_inst = nullptr;
+    bt::Out *pin_out = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, int> graph_grid;  // blocks of each graph's launch
+    long long graph_launches = 0;
 };
 
 namespace {
@@ -890,6 +900,12 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
     b->d_queue = (int *)balloc(b, sizeof(int) * 4);
     b->d_out = (bt::Out *)balloc(b, sizeof(bt::Out) * ninst);
     if (!b->d_sys || !b->d_inst || !b->d_order || !b->d_queue || !b->d_out) return fail(F3R_ERR_NOMEM);
+    if (cudaHostAlloc((void **)&b->pin_inst, sizeof(bt::Inst) * ninst, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&b->pin_out, sizeof(bt::Out) * ninst, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(F3R_ERR_NOMEM);
+    }
+    std::memset(b->pin_out, 0, sizeof(bt::Out) * ninst);
     cudaMemcpyAsync(b->d_sys, hs.data(), sizeof(bt::Sys) * nsys, cudaMemcpyHostToDevice, s);
     // the persistent launch's instances, largest first
     for (int q = 0; q < ninst; ++q)
@@ -912,11 +928,21 @@ f3r_status f3r_batched_set_cluster(f3r_batch *b, int cluster_size) {
     return F3R_OK;
 }
 
+f3r_status f3r_batched_set_shape(f3r_batch *b, int cluster_size, int threads) {
+    if (!b || (threads != 256 && threads != 512)) return F3R_ERR_ARG;
+    const f3r_status st = f3r_batched_set_cluster(b, cluster_size);
+    if (st != F3R_OK) return st;
+    b->threads = threads;
+    return F3R_OK;
+}
+
 }  // extern "C"
 
 namespace {
 // The persistent launch over the instances of the small systems; their
-// statuses go to st[q] (and res[q] when given).
+// statuses go to st[q] (and res[q] when given).  Replayed as a CUDA graph
+// (one per cluster size and block size): the instances' b and x pointers go
+// through a pinned host table that the graph copies to the device.
 f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, f3r_batch_result *res,
                         std::vector<int> &st, void *stream) {
     const int nsmall = (int)b->small.size();
@@ -932,32 +958,57 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
         b->h_inst[q].b = B[q];
         b->h_inst[q].x = X[q];
     }
-    cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(bt::Inst) * ninst, cudaMemcpyHostToDevice, s);
-    cudaMemsetAsync(b->d_queue, 0, sizeof(int) * 4, s);
-    cudaLaunchConfig_t cfg = {};
-    const int cl = b->cluster;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cl;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(bt::kBT, 1, 1);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int ncl = 0;
-    cfg.gridDim = dim3(cl, 1, 1);
-    if (cudaOccupancyMaxActiveClusters(&ncl, (void *)bt::k_batch, &cfg) != cudaSuccess || ncl < 1) {
-        cudaGetLastError();
-        ncl = 1;
+    // the graph reads the table from pinned memory when it runs
+    std::memcpy(b->pin_inst, b->h_inst.data(), sizeof(bt::Inst) * ninst);
+    const int cl = b->cluster, nt = b->threads;
+    const int key = cl * 1024 + nt;
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cl;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(nt, 1, 1);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        cfg.gridDim = dim3(cl, 1, 1);
+        if (cudaOccupancyMaxActiveClusters(&ncl, (void *)bt::k_batch, &cfg) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            ncl = 1;
+        }
+        ncl = std::min(ncl, nsmall);
+        cfg.gridDim = dim3(ncl * cl, 1, 1);
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemcpyAsync(b->d_inst, b->pin_inst, sizeof(bt::Inst) * ninst, cudaMemcpyHostToDevice, s);
+            cudaMemsetAsync(b->d_queue, 0, sizeof(int) * 4, s);
+            cudaLaunchKernelEx(&cfg, bt::k_batch, (const bt::Sys *)b->d_sys, (const bt::Inst *)b->d_inst,
+                               (const int *)b->d_order, nsmall, b->P, b->d_queue, b->d_out);
+            cudaMemcpyAsync(b->pin_out, b->d_out, sizeof(bt::Out) * ninst, cudaMemcpyDeviceToHost, s);
+            e = cudaStreamEndCapture(s, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return F3R_ERR_CUDA;
+        }
+        it = b->graphs.emplace(key, ge).first;
+        b->graph_grid[key] = ncl * cl;
     }
-    ncl = std::min(ncl, nsmall);
-    cfg.gridDim = dim3(ncl * cl, 1, 1);
-    b->grid = ncl * cl;
+    b->grid = b->graph_grid[key];
     cudaEventRecord(e0, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, bt::k_batch, (const bt::Sys *)b->d_sys, (const bt::Inst *)b->d_inst,
-                                       (const int *)b->d_order, nsmall, b->P, b->d_queue, b->d_out);
+    cudaError_t e = cudaGraphLaunch(it->second, s);
+    b->graph_launches++;
     cudaEventRecord(e1, s);
     if (e != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
         cudaEventDestroy(e0);
@@ -967,8 +1018,7 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
     }
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
-    std::vector<bt::Out> ho(ninst);
-    cudaMemcpy(ho.data(), b->d_out, sizeof(bt::Out) * ninst, cudaMemcpyDeviceToHost);
+    const bt::Out *ho = b->pin_out;
     for (int q : b->small) {
         st[q] = ho[q].status;
         if (res) {
@@ -981,6 +1031,7 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
             res[q].t_solve_ms = ms;
             res[q].system = b->inst_sys[q];
             res[q].rhs = b->inst_rhs[q];
+            res[q].path = 0;
         }
     }
     cudaEventRecord(e1, s);
@@ -1016,6 +1067,7 @@ f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const
             res[q].t_solve_ms = ss.t_solve_ms;
             res[q].system = b->inst_sys[q];
             res[q].rhs = b->inst_rhs[q];
+            res[q].path = 1;
         }
     }
     const f3r_status e = launch_small(b, B, X, res, st, stream);
@@ -1026,20 +1078,23 @@ f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const
 }
 
 // Autotuner of the batched launch shape: time one outer iteration of the
-// persistent launch's instances (from x0 = 0) for every cluster size that
-// fits, keep the fastest.  X is zeroed again on return.
+// persistent launch's instances (from x0 = 0) for every team shape -- blocks
+// per instance (the cluster size: 1, 2, 4, 8) times threads per block (256,
+// 512), i.e. the rows each thread of a team covers -- and keep the fastest.
+// X is zeroed again on return.  The graphs made while timing stay cached.
 f3r_status f3r_batched_autotune(f3r_batch *b, const double *const *B, double *const *X, int *chosen, void *stream) {
     if (!b || !B || !X) return F3R_ERR_ARG;
     const int saved_outer = b->P.max_outer;
-    const int cand[4] = {1, 2, 4, 8};
+    const int cand[8][2] = {{1, 256}, {1, 512}, {2, 256}, {2, 512}, {4, 256}, {4, 512}, {8, 256}, {8, 512}};
     float best = 3.0e38f;
-    int best_c = b->cluster;
+    int best_c = b->cluster, best_t = b->threads;
     const int ninst = (int)b->h_inst.size();
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int ci = 0; ci < 4; ++ci) {
-        b->cluster = cand[ci];
+    for (int ci = 0; ci < 8; ++ci) {
+        b->cluster = cand[ci][0];
+        b->threads = cand[ci][1];
         b->P.max_outer = 1;
         for (int q : b->small) cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
         cudaEventRecord(e0, b->cs);
@@ -1053,11 +1108,17 @@ f3r_status f3r_batched_autotune(f3r_batch *b, const double *const *B, double *co
         cudaEventElapsedTime(&ms, e0, e1);
         if ((st == F3R_OK || st == F3R_NOT_CONVERGED) && ms < best) {
             best = ms;
-            best_c = cand[ci];
+            best_c = cand[ci][0];
+            best_t = cand[ci][1];
         }
     }
     b->P.max_outer = saved_outer;
     b->cluster = best_c;
+    b->threads = best_t;
+    // the graphs captured while tuning hold max_outer = 1: drop them
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    b->graph_grid.clear();
     for (int q = 0; q < ninst; ++q) cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
     cudaStreamSynchronize(b->cs);
     cudaEventDestroy(e0);
@@ -1067,6 +1128,29 @@ f3r_status f3r_batched_autotune(f3r_batch *b, const double *const *B, double *co
 }
 
 int f3r_batched_instances(const f3r_batch *b) { return b ? (int)b->h_inst.size() : 0; }
+
+f3r_status f3r_batched_info(const f3r_batch *b, int64_t *out) {
+    if (!b || !out) return F3R_ERR_ARG;
+    long long rows_small = 0, rows_full = 0, n_full = 0;
+    for (size_t q = 0; q < b->h_inst.size(); ++q) {
+        const long long n = b->sys[b->inst_sys[q]]->n;
+        if (b->full[b->inst_sys[q]]) {
+            rows_full += n;
+            ++n_full;
+        } else {
+            rows_small += n;
+        }
+    }
+    out[0] = b->cluster;
+    out[1] = b->threads;
+    out[2] = (int64_t)b->small.size();
+    out[3] = n_full;
+    out[4] = rows_small;
+    out[5] = rows_full;
+    out[6] = b->grid;
+    out[7] = b->graph_launches;
+    return F3R_OK;
+}
 
 int64_t f3r_batched_device_bytes(const f3r_batch *b) {
     if (!b) return 0;
@@ -1085,11 +1169,12 @@ void f3r_destroy_batched(f3r_batch *b) {
     }
     for (f3r_ctx *h : b->full)
         if (h) f3r_destroy(h);
+    if (b->cs) cudaStreamSynchronize(b->cs);
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     for (void *p : b->allocs) cudaFree(p);
-    if (b->cs) {
-        cudaStreamSynchronize(b->cs);
-        cudaStreamDestroy(b->cs);
-    }
+    if (b->pin_inst) cudaFreeHost(b->pin_inst);
+    if (b->pin_out) cudaFreeHost(b->pin_out);
+    if (b->cs) cudaStreamDestroy(b->cs);
     delete b;
 }
 

@@ -61,7 +61,7 @@ class SystemDesc(C.Structure):
 class BatchResult(C.Structure):
     _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("restarts", C.c_int),
                 ("rel_res_true", C.c_double), ("m_applies", C.c_int64), ("r_calls", C.c_int64),
-                ("t_solve_ms", C.c_double), ("system", C.c_int), ("rhs", C.c_int)]
+                ("t_solve_ms", C.c_double), ("system", C.c_int), ("rhs", C.c_int), ("path", C.c_int)]
 
 
 _lib = None
@@ -108,6 +108,8 @@ def lib():
         L.f3r_batched_autotune.restype = C.c_int
         L.f3r_batched_instances.argtypes = [vp]
         L.f3r_batched_instances.restype = C.c_int
+        L.f3r_batched_set_shape.argtypes = [vp, C.c_int, C.c_int]
+        L.f3r_batched_info.argtypes = [vp, C.POINTER(C.c_int64)]
         L.f3r_batched_device_bytes.argtypes = [vp]
         L.f3r_batched_device_bytes.restype = C.c_int64
         L.f3r_destroy_batched.argtypes = [vp]
@@ -415,8 +417,20 @@ class BatchedSolver:
     def set_cluster(self, k: int):
         _check(lib().f3r_batched_set_cluster(self.h, k), "f3r_batched_set_cluster")
 
+    def set_shape(self, cluster: int, threads: int):
+        _check(lib().f3r_batched_set_shape(self.h, cluster, threads), "f3r_batched_set_shape")
+
+    def info(self) -> dict:
+        """How the batch runs (f3r_batched_info)."""
+        out = (C.c_int64 * 8)()
+        _check(lib().f3r_batched_info(self.h, out), "f3r_batched_info")
+        keys = ("cluster", "threads", "instances_launch", "instances_single", "rows_launch", "rows_single",
+                "grid", "graph_launches")
+        return {k: int(v) for k, v in zip(keys, out)}
+
     def autotune(self, B, X, stream=None) -> int:
-        """Pick the cluster size by timing one outer iteration of the batch; X is zeroed."""
+        """Pick the team shape (cluster size, threads per block) by timing one
+        outer iteration of the batch; returns the cluster size; X is zeroed."""
         bp = (C.c_void_p * self.ninst)(*[b.data_ptr() for b in B])
         xp = (C.c_void_p * self.ninst)(*[x.data_ptr() for x in X])
         ch = C.c_int()

@@ -96,3 +96,56 @@ def test_batched_split_large_systems_to_single_path(batch):
             assert torch.equal(xs, Xs[q])
             s.close()
     bs.close()
+
+
+def _instances(batch):
+    Bs, Xs, meta = [], [], []
+    for k, (p, B) in enumerate(batch):
+        for r in range(B.shape[0]):
+            Bs.append(dev(B[r]))
+            Xs.append(torch.zeros(p.n, dtype=torch.float64, device="cuda"))
+            meta.append((k, r))
+    return Bs, Xs, meta
+
+
+def _check(batch, Xs, meta, res):
+    for q, (k, r) in enumerate(meta):
+        p, B = batch[k]
+        rel = np.linalg.norm(B[r] - p.to_scipy() @ Xs[q].cpu().numpy()) / np.linalg.norm(B[r])
+        assert res[q].status == f3r.OK and rel < 1e-9, (q, rel)
+        assert res[q].path == 0  # every system here is below batch_split: the persistent launch
+
+
+@pytest.mark.parametrize("cluster,threads", [(2, 256), (4, 512), (1, 256)])
+def test_batched_team_shapes_and_graph_replay(batch, cluster, threads):
+    """Every team shape solves every instance; the second solve replays the
+    captured graph with other x buffers (the pinned table carries them)."""
+    systems = [(dev(p.rowptr), dev(p.colidx), dev(p.val), B.shape[0]) for p, B in batch]
+    bs = f3r.BatchedSolver(systems, f3r.default_params())
+    bs.set_shape(cluster, threads)
+    for rep in range(2):
+        Bs, Xs, meta = _instances(batch)
+        code, res = bs.solve(Bs, Xs)
+        torch.cuda.synchronize()
+        assert code == f3r.OK
+        _check(batch, Xs, meta, res)
+    info = bs.info()
+    assert (info["cluster"], info["threads"]) == (cluster, threads)
+    assert info["graph_launches"] == 2 and info["instances_launch"] == len(meta) and info["instances_single"] == 0
+    assert info["grid"] % cluster == 0 and info["grid"] > 0
+    bs.close()
+
+
+def test_batched_autotune_picks_a_shape(batch):
+    systems = [(dev(p.rowptr), dev(p.colidx), dev(p.val), B.shape[0]) for p, B in batch]
+    bs = f3r.BatchedSolver(systems, f3r.default_params())
+    Bs, Xs, meta = _instances(batch)
+    chosen = bs.autotune(Bs, Xs)
+    info = bs.info()
+    assert chosen == info["cluster"] and info["cluster"] in (1, 2, 4, 8) and info["threads"] in (256, 512)
+    assert all(float(x.abs().max()) == 0.0 for x in Xs)  # X zeroed again
+    code, res = bs.solve(Bs, Xs)
+    torch.cuda.synchronize()
+    assert code == f3r.OK
+    _check(batch, Xs, meta, res)
+    bs.close()
