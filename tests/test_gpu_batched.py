@@ -149,3 +149,25 @@ def test_batched_autotune_picks_a_shape(batch):
     assert code == f3r.OK
     _check(batch, Xs, meta, res)
     bs.close()
+
+
+def test_batched_large_systems_next_to_the_launch(batch):
+    """With batch_split below some systems' size, those instances run on the
+    single-system path while the persistent launch runs beside them: every
+    instance is still solved, each path reports itself."""
+    systems = [(dev(p.rowptr), dev(p.colidx), dev(p.val), B.shape[0]) for p, B in batch]
+    ns = sorted(p.n for p, _ in batch)
+    split = ns[len(ns) // 2]
+    bs = f3r.BatchedSolver(systems, f3r.default_params(batch_split=split))
+    Bs, Xs, meta = _instances(batch)
+    code, res = bs.solve(Bs, Xs)
+    torch.cuda.synchronize()
+    assert code == f3r.OK
+    info = bs.info()
+    assert info["instances_single"] > 0 and info["instances_launch"] > 0
+    for q, (k, r) in enumerate(meta):
+        p, B = batch[k]
+        rel = np.linalg.norm(B[r] - p.to_scipy() @ Xs[q].cpu().numpy()) / np.linalg.norm(B[r])
+        assert res[q].status == f3r.OK and rel < 1e-9, (q, rel)
+        assert res[q].path == (1 if p.n >= split else 0)
+    bs.close()
