@@ -115,8 +115,8 @@ def preset(name: str, **kw) -> Params:
 
     fp16-F3R / fp32-F3R / fp64-F3R (Sec. 5), bf16-F3R (16-bit brain float in
     place of fp16 with per-row scaling), fgmres64 (restarted fp64 FGMRES(64)
-    with M), and the depth variants F2 / F3 / F4 of Table 4 restricted to
-    fp32 or fp64 vectors.
+    with M), and the depth variants of Table 4: F2, F3, fp16-F3 (the inner
+    F8 with fp16 vectors) and F4 (its F2 with fp16 vectors).
     """
     if name == "fp16-F3R":
         p = params()
@@ -134,8 +134,11 @@ def preset(name: str, **kw) -> Params:
         p = params(nlevels=2, m=[100, 64, 0, 0], a_prec=[F64, F32, F32, F32], rich_m=0, m_prec=F16)
     elif name == "F3":
         p = params(nlevels=3, m=[100, 8, 8, 0], rich_m=0, m_prec=F16)
+    elif name == "fp16-F3":
+        p = params(nlevels=3, m=[100, 8, 8, 0], v_prec=[F64, F32, F16, F32], rich_m=0, m_prec=F16)
     elif name == "F4":
-        p = params(nlevels=4, m=[100, 8, 4, 2], a_prec=[F64, F32, F16, F16], rich_m=0, m_prec=F16)
+        p = params(nlevels=4, m=[100, 8, 4, 2], a_prec=[F64, F32, F16, F16], v_prec=[F64, F32, F32, F16],
+                   rich_m=0, m_prec=F16)
     else:
         raise KeyError(name)
     for k, v in kw.items():

@@ -480,10 +480,17 @@ struct Nest {
      * convergence check -- Sec. 4.2), or, with inner_rtol > 0 at the innermost
      * FGMRES level, until its residual estimate falls below inner_rtol * beta.
      * The weight counter c_ntr counts the scheduled Richardson calls: those of
-     * iterations a level does not run are added when it ends. */
+     * iterations a level does not run are added when it ends.
+     * A level with 16-bit vectors (v_prec F16 / BF16, the fp16 levels of
+     * Table 4) computes in fp32 and rounds what it stores -- V[0], each
+     * normalised V[j+1] and each Z[j] = M V[j] -- to that format; w and the
+     * small Hessenberg problem stay in fp32. */
     template <class T>
     void fgmres_inner(int d, const T *v, T *z) {
         const int n = P.n, m = prm.m[d];
+        const int vs = prm.v_prec[d];
+        const bool v16 = vs == ORC_F16 || vs == ORC_BF16;
+        auto store = [&](T x) { return v16 ? (T)rnd_prec(vs, (double)x) : x; };
         T beta = std::sqrt(dot_t(v, v, n));
         if (!std::isfinite(beta)) {
             for (int i = 0; i < n; ++i) z[i] = (T)NAN;
@@ -502,11 +509,13 @@ struct Nest {
         std::vector<T> w(n), hcol(m + 1), Hraw((size_t)(m + 1) * m, T(0));
         Givens<T> G(m);
         T inv = (T)1 / beta;
-        for (int i = 0; i < n; ++i) V[0][i] = v[i] * inv;
+        for (int i = 0; i < n; ++i) V[0][i] = store(v[i] * inv);
         G.g[0] = beta;
         int kdim = 0;
         for (int j = 0; j < m; ++j) {
             apply_below<T>(d, V[j].data(), Z[j].data());
+            if (v16)
+                for (int i = 0; i < n; ++i) Z[j][i] = store(Z[j][i]);
             ran = j + 1;
             spmv_t<T>(P, prm.a_prec[d], Z[j].data(), w.data());
             cgs<T>(V, j, w, prm.cgs_passes, hcol);
@@ -519,7 +528,7 @@ struct Nest {
             if (!(hn > 0)) break;  // exact breakdown: the subspace holds the solution
             if (adaptive && std::abs(G.g[j + 1]) <= rtol * beta) break;  // level residual small enough
             T invh = (T)1 / hn;
-            for (int i = 0; i < n; ++i) V[j + 1][i] = w[i] * invh;
+            for (int i = 0; i < n; ++i) V[j + 1][i] = store(w[i] * invh);
         }
         st->c_ntr += (int64_t)(m - ran) * calls_below(d);
         std::vector<T> y = G.solve(kdim);

@@ -28,7 +28,9 @@ typedef struct {
     int nlevels;        /* number of FGMRES levels, 1..4; level 0 is the outer fp64 solver */
     int m[4];           /* iterations of each FGMRES level (m[0] = restart length m1) */
     int a_prec[4];      /* precision of A used by each level (level 0: ORC_F64, original A) */
-    int v_prec[4];      /* vector precision of each level: ORC_F64 or ORC_F32 */
+    int v_prec[4];      /* vector precision of each level: ORC_F64 or ORC_F32; ORC_F16 / ORC_BF16
+                           (fp32 arithmetic, stored vectors rounded) at the innermost
+                           FGMRES level when it applies M (rich_m = 0) */
     int rich_m;         /* Richardson iterations m4; 0 = no Richardson level */
     int rich_a_prec;    /* precision of A inside Richardson */
     int rich_v_prec;    /* precision of Richardson vectors (F16, BF16, F32, F64) */
