@@ -60,7 +60,11 @@ typedef struct {
     int m[4];           /* iterations per FGMRES level; m[0] is the restart length m1 (<= 128),
                            inner levels <= 15 */
     int a_prec[4];      /* precision of A used by each level; a_prec[0] must be F3R_F64 */
-    int v_prec[4];      /* vector precision per level: F3R_F64 or F3R_F32 (v_prec[0] = F3R_F64) */
+    int v_prec[4];      /* vector precision per level: F3R_F64 or F3R_F32 (v_prec[0] = F3R_F64);
+                           F3R_F16 / F3R_BF16 at the innermost FGMRES level when it applies M
+                           (rich_m = 0; Table 4's fp16 levels): fp32 arithmetic and fp32 arrays
+                           whose stored V and Z values are rounded to that format, so the
+                           level's f3r_apply / f3r_get_basis vectors are float */
     int rich_m;         /* Richardson iterations m4 (0 = the innermost FGMRES applies M), <= 8 */
     int rich_a_prec;    /* precision of A inside Richardson */
     int rich_v_prec;    /* precision of Richardson vectors: F16, BF16, F32 or F64 */

@@ -184,7 +184,17 @@ bool launch_cgs_fused(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_
 bool launch_outer_cgs_fused(Ctx &c, cudaStream_t s);
 bool launch_f3_step(Ctx &c, int d, int j, bool last, bool update, cudaStream_t s);
 void launch_combine(Ctx &c, int d, const OutSlot &o, cudaStream_t s);
-void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s);
+// vround: the output is a level's stored Z[j] rounded to 16 bits (vround_of)
+void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s,
+              int vround = 0);
+// 1 / 2 when FGMRES level d stores its vectors in fp16 / bf16 (Table 4's fp16 levels), else 0
+inline int vround_of(const Ctx &c, int d) {
+    if (d < 1) return 0;
+    const int v = c.prm.v_prec[d];
+    return v == F3R_F16 ? 1 : (v == F3R_BF16 ? 2 : 0);
+}
+// bytes per element of level d's vector arrays (16-bit levels keep fp32 arrays)
+inline int level_vec_bytes(const Ctx &c, int d) { return c.prm.v_prec[d] == F3R_F64 ? 8 : 4; }
 void launch_outer_residual(Ctx &c, const double *b, const double *x, bool compute_nb, cudaStream_t s);
 bool launch_outer_step(Ctx &c, cudaStream_t s);
 void launch_outer_finish(Ctx &c, double *x, cudaStream_t s);

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8 && kFusedThreads <= 
                 TC cacc[2] = {(TC)0, (TC)0};
                 TC *cx = co.x + r0;
                 for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-                    const T v = mul_rn(ws[i], inv);
+                    const T v = vstore(L.vround, mul_rn(ws[i], inv));
                     const TC c = Store<TC>::from(v);
                     out[i] = v;
                     cx[i] = c;
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8 && kFusedThreads <= 
                     const Pack<T, N> sv = ldp<T, N>(ws + (size_t)q * N);
                     Pack<T, N> op;
 #pragma unroll
-                    for (int e = 0; e < N; ++e) op.v[e] = mul_rn(sv.v[e], inv);
+                    for (int e = 0; e < N; ++e) op.v[e] = vstore(L.vround, mul_rn(sv.v[e], inv));
                     stp<T, N>(out + (size_t)q * N, op);
                     if constexpr (CHILD == CHILD_R) {
                         Pack<TC, N> cp;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8 && kFusedThreads <= 
                     }
                 }
                 for (int i = nq * N + threadIdx.x; i < cnt; i += blockDim.x) {
-                    const T v = mul_rn(ws[i], inv);
+                    const T v = vstore(L.vround, mul_rn(ws[i], inv));
                     out[i] = v;
                     if constexpr (CHILD == CHILD_R) co.x[r0 + i] = Store<TC>::from(mul_rn(sig, v));
                 }

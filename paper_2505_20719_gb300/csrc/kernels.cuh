@@ -43,6 +43,7 @@ template <class T> struct LevelDev {
     T *scal;
     int *flags;        // base of all levels' flags; this level's at flags[4*depth]
     const int *jptr;   // outer level: iteration index read on the device (graph replay)
+    int vround = 0;    // the level's stored vectors V, Z rounded to 1: fp16, 2: bf16 (Table 4's fp16 levels)
     __device__ T *H() const { return scal + scal_H(m); }
     __device__ T *cs() const { return scal + scal_cs(m); }
     __device__ T *sn() const { return scal + scal_sn(m); }
@@ -53,6 +54,14 @@ template <class T> struct LevelDev {
     __device__ T *misc() const { return scal + scal_misc(m); }
     __device__ int *fl() const { return flags + 4 * depth; }
 };
+
+// a value of a level's stored vector V or Z: rounded to 16 bits at the levels
+// that store their vectors in fp16 / bf16 (kept in fp32 arrays)
+template <class T> __device__ __forceinline__ T vstore(int vround, T v) {
+    if (vround == 1) return rnd<h16>(v);
+    if (vround == 2) return rnd<b16>(v);
+    return v;
+}
 
 // true when level `upto` or one of its inner ancestors (levels >= 1) stopped
 __device__ __forceinline__ bool stopped(const int *flags, int upto) {
@@ -334,7 +343,7 @@ __global__ void __launch_bounds__(kVecBlock) k_normalize(LevelDev<T> L, const T 
     if constexpr (CHILD == CHILD_F) {
         TC acc[2] = {(TC)0, (TC)0};
         auto one = [&](int i, T sv) {
-            const T v = mul_rn(sv, inv);
+            const T v = vstore(L.vround, mul_rn(sv, inv));
             const TC c = co.dsc ? Store<TC>::from(mul_rn(co.dsc[i], (double)v)) : Store<TC>::from(v);
             acc[0] = fma_rn(c, c, acc[0]);
             acc[1] = fmax(acc[1], fabs(c));
@@ -403,7 +412,7 @@ __global__ void __launch_bounds__(kVecBlock) k_normalize(LevelDev<T> L, const T 
                 if (q < nq) {
                     Pack<T, N> op;
 #pragma unroll
-                    for (int e = 0; e < N; ++e) op.v[e] = mul_rn(sp[u].v[e], inv);
+                    for (int e = 0; e < N; ++e) op.v[e] = vstore(L.vround, mul_rn(sp[u].v[e], inv));
                     stp<T, N>(out + (size_t)q * N, op);
                     if constexpr (CHILD == CHILD_R) {
                         Pack<TC, N> cp;
@@ -415,7 +424,7 @@ __global__ void __launch_bounds__(kVecBlock) k_normalize(LevelDev<T> L, const T 
             }
         });
         for (int i = nq * N + tid; i < L.n; i += nth) {
-            const T v = mul_rn(src[i], inv);
+            const T v = vstore(L.vround, mul_rn(src[i], inv));
             out[i] = v;
             if constexpr (CHILD == CHILD_R) co.x[i] = Store<TC>::from(mul_rn(sig, v));
         }
@@ -484,12 +493,12 @@ __global__ void __launch_bounds__(kVecBlock) k_combine(LevelDev<T> L, TP *out_ba
 template <class T, class MS>
 __global__ void __launch_bounds__(kBlock) k_apply_M(const MS *__restrict__ mv, const T *__restrict__ v_base,
                                                     const int *in_j, int ld, T *z, int n, const int *flags,
-                                                    int check_depth, long long *m_count) {
+                                                    int check_depth, long long *m_count, int vround) {
     pdl_enter();
     if (stopped(flags, check_depth)) return;
     const T *__restrict__ v = v_base + (in_j ? (size_t)(*in_j) * ld : 0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        z[i] = mul_rn(to_c<T>(mv[i]), v[i]);
+        z[i] = vstore(vround, mul_rn(to_c<T>(mv[i]), v[i]));
     if (blockIdx.x == 0 && threadIdx.x == 0 && m_count) atomicAdd((unsigned long long *)m_count, 1ull);
 }
 

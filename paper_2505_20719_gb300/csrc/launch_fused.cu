@@ -64,6 +64,7 @@ template <class T> LevelDev<T> levdev_inner(Ctx &c, int d) {
     L.scal = (T *)c.L[d].scal;
     L.flags = c.flags;
     L.jptr = nullptr;
+    L.vround = vround_of(c, d);
     return L;
 }
 

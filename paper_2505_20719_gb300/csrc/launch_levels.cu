@@ -19,6 +19,7 @@ template <class T> static LevelDev<T> levdev(Ctx &c, int d) {
     L.scal = (T *)c.L[d].scal;
     L.flags = c.flags;
     L.jptr = (d == 0) ? c.jdev : nullptr;
+    L.vround = vround_of(c, d);
     return L;
 }
 
@@ -260,7 +261,8 @@ void launch_combine(Ctx &c, int d, const OutSlot &o, cudaStream_t s) {
 }
 
 // -------------------------------------------------------------------- M
-void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s) {
+void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s,
+              int vround) {
     (void)j;
     const bool t64 = c.L[d].v_prec == F3R_F64;
     unsigned long long *cnt = c.counters;
@@ -269,17 +271,17 @@ void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, 
     prof_begin(c, PK_M, d, s);
     if (t64) {
         switch (c.prm.m_prec) {
-            case F3R_F64: launch_pdl(k_apply_M<double, double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            case F3R_F32: launch_pdl(k_apply_M<double, float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            case F3R_F16: launch_pdl(k_apply_M<double, h16>, dim3(c.G), dim3(kBlock), 0, s, (const h16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            default: launch_pdl(k_apply_M<double, b16>, dim3(c.G), dim3(kBlock), 0, s, (const b16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F64: launch_pdl(k_apply_M<double, double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt, vround); break;
+            case F3R_F32: launch_pdl(k_apply_M<double, float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt, vround); break;
+            case F3R_F16: launch_pdl(k_apply_M<double, h16>, dim3(c.G), dim3(kBlock), 0, s, (const h16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt, vround); break;
+            default: launch_pdl(k_apply_M<double, b16>, dim3(c.G), dim3(kBlock), 0, s, (const b16 *)c.mvec, (const double *)in, ij, c.ld, (double *)out, n, c.flags, check_depth, (long long *)cnt, vround); break;
         }
     } else {
         switch (c.prm.m_prec) {
-            case F3R_F32: launch_pdl(k_apply_M<float, float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            case F3R_F16: launch_pdl(k_apply_M<float, h16>, dim3(c.G), dim3(kBlock), 0, s, (const h16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            case F3R_BF16: launch_pdl(k_apply_M<float, b16>, dim3(c.G), dim3(kBlock), 0, s, (const b16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
-            default: launch_pdl(k_apply_M<float, double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt); break;
+            case F3R_F32: launch_pdl(k_apply_M<float, float>, dim3(c.G), dim3(kBlock), 0, s, (const float *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt, vround); break;
+            case F3R_F16: launch_pdl(k_apply_M<float, h16>, dim3(c.G), dim3(kBlock), 0, s, (const h16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt, vround); break;
+            case F3R_BF16: launch_pdl(k_apply_M<float, b16>, dim3(c.G), dim3(kBlock), 0, s, (const b16 *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt, vround); break;
+            default: launch_pdl(k_apply_M<float, double>, dim3(c.G), dim3(kBlock), 0, s, (const double *)c.mvec, (const float *)in, ij, c.ld, (float *)out, n, c.flags, check_depth, (long long *)cnt, vround); break;
         }
     }
     prof_end(c, s);

@@ -59,6 +59,10 @@ f3r_status check_params(const f3r_params &p) {
             if (p.a_prec[d] != F3R_F64) return F3R_ERR_UNSUPPORTED;
         } else if (p.v_prec[d] == F3R_F32) {
             if (p.a_prec[d] != F3R_F32 && p.a_prec[d] != F3R_F16 && p.a_prec[d] != F3R_BF16) return F3R_ERR_UNSUPPORTED;
+        } else if (p.v_prec[d] == F3R_F16 || p.v_prec[d] == F3R_BF16) {
+            // 16-bit stored vectors (Table 4): the innermost level, applying M itself
+            if (d != p.nlevels - 1 || p.rich_m != 0) return F3R_ERR_UNSUPPORTED;
+            if (p.a_prec[d] != F3R_F32 && p.a_prec[d] != F3R_F16 && p.a_prec[d] != F3R_BF16) return F3R_ERR_UNSUPPORTED;
         } else {
             return F3R_ERR_UNSUPPORTED;
         }
@@ -167,7 +171,7 @@ void run_level(Ctx &c, int d, const OutSlot &out, long long &pos, cudaStream_t s
             launch_rich_call(c, is_update(c, pos), (int)pos, zslot(c, d, j), misc_of(c, d), s);
             ++pos;
         } else {
-            launch_M(c, d, j, vslot(c, d, j), zslot(c, d, j), d, false, s);
+            launch_M(c, d, j, vslot(c, d, j), zslot(c, d, j), d, false, s, vround_of(c, d));
         }
         launch_spmv_dots(c, d, j, s);
         if (launch_cgs_fused(c, d, j, j == L.m - 1, j < L.m - 1, s)) continue;
@@ -408,7 +412,7 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
         L.a_prec = prm.a_prec[d];
         L.v_prec = prm.v_prec[d];
         L.child = (d + 1 < prm.nlevels) ? CHILD_F : (prm.rich_m > 0 ? CHILD_R : CHILD_M);
-        const size_t eb = (size_t)prec_bytes(L.v_prec);
+        const size_t eb = (size_t)level_vec_bytes(c, d);
         L.V = dalloc(c, eb * c.ld * (L.m + 1));
         L.Z = dalloc(c, eb * c.ld * L.m);
         L.w = dalloc(c, eb * c.ld);
@@ -678,7 +682,7 @@ f3r_status f3r_get_basis(f3r_ctx *h, int level, int k, void *out, void *stream) 
     if (!h || !out) return F3R_ERR_ARG;
     Ctx &c = h->c;
     if (level < 0 || level >= c.prm.nlevels || k < 0 || k > c.L[level].m) return F3R_ERR_ARG;
-    const size_t eb = (size_t)prec_bytes(c.L[level].v_prec);
+    const size_t eb = (size_t)level_vec_bytes(c, level);
     const char *src = (const char *)c.L[level].V + (size_t)k * c.ld * eb;
     cudaStream_t s = (cudaStream_t)stream;
     // ordered after the context's own work (the solve that left the basis)

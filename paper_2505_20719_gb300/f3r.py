@@ -182,8 +182,9 @@ def default_params(**kw) -> Params:
 def preset(name: str, **kw) -> Params:
     """Named configurations: fp16-F3R (Table 1), bf16-F3R (bf16 inner storage
     with per-row scaling), fp32-F3R and fp64-F3R (Sec. 5), fgmres64 (fp64
-    restarted FGMRES(64) with M, Sec. 5), and the depth variants F3 and F4 of
-    Table 4."""
+    restarted FGMRES(64) with M, Sec. 5), and the depth variants F3, fp16-F3
+    and F4 of Table 4.  Their fp16-vector levels compute in fp32 and round
+    every stored V and Z value to fp16 (held in fp32 arrays)."""
     if name == "fp16-F3R":
         p = default_params()
     elif name == "bf16-F3R":
@@ -199,10 +200,13 @@ def preset(name: str, **kw) -> Params:
     elif name == "F3":
         # Table 4: (F100, F8, F8, M), the inner F8 with fp16 A and fp32 vectors
         p = default_params(nlevels=3, m=[100, 8, 8, 0], rich_m=0, m_prec=F16)
+    elif name == "fp16-F3":
+        # Table 4: F3 with fp16 vectors in the inner F8
+        p = default_params(nlevels=3, m=[100, 8, 8, 0], v_prec=[F64, F32, F16, F32], rich_m=0, m_prec=F16)
     elif name == "F4":
-        # Table 4: (F100, F8, F4, F2, M) with fp32 vectors in F2 (the GPU keeps
-        # inner FGMRES vectors in fp32)
-        p = default_params(nlevels=4, m=[100, 8, 4, 2], a_prec=[F64, F32, F16, F16], rich_m=0, m_prec=F16)
+        # Table 4: (F100, F8, F4, F2, M), the F2 with fp16 A and fp16 vectors
+        p = default_params(nlevels=4, m=[100, 8, 4, 2], a_prec=[F64, F32, F16, F16], v_prec=[F64, F32, F32, F16],
+                           rich_m=0, m_prec=F16)
     else:
         raise KeyError(name)
     return _set(p, kw)
