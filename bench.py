@@ -421,6 +421,7 @@ def run_sweep(args):
               for t in (0.4, 0.6, 0.8)]
     cases += [(f"approximate inverse M, alpha={a}", "fp16-F3R", {"precond": f3r.PC_AINV, "ainv_alpha": a})
               for a in (1.0, 1.5)]
+    cases += [("depth F2 (F100,F64,M)", "F2", {}), ("depth fp16-F2 (inner F64 in fp16)", "fp16-F2", {})]
     cases += [("depth F3 (F100,F8,F8,M)", "F3", {}), ("depth fp16-F3 (inner F8 fp16 vectors)", "fp16-F3", {}),
               ("depth F4 (F100,F8,F4,F2,M)", "F4", {}),
               ("fp32-F3R", "fp32-F3R", {}), ("bf16-F3R", "bf16-F3R", {})]

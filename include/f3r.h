@@ -166,7 +166,8 @@ f3r_status f3r_spmv(f3r_ctx *ctx, int p, int vp, const void *x, void *y, void *s
  * x and z are device pointers of n elements. */
 f3r_status f3r_apply(f3r_ctx *ctx, int level, const void *x, void *z, void *stream);
 
-/* Copy basis vector V[k] (0 <= k <= m of that level) of FGMRES level `level`
+/* Copy basis vector V[k] (0 <= k <= m of that level; an inner level, which
+ * ends at its m-th Givens step, never forms V[m]) of FGMRES level `level`
  * as the context's last call left it -- for level 0 the last restart cycle of
  * the last f3r_solve: the normalised residual (k = 0) and the Arnoldi vectors
  * of the outer fp64 FGMRES (Sec. 4.2) -- into `out` (n elements in the

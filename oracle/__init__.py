@@ -115,8 +115,9 @@ def preset(name: str, **kw) -> Params:
 
     fp16-F3R / fp32-F3R / fp64-F3R (Sec. 5), bf16-F3R (16-bit brain float in
     place of fp16 with per-row scaling), fgmres64 (restarted fp64 FGMRES(64)
-    with M), and the depth variants of Table 4: F2, F3, fp16-F3 (the inner
-    F8 with fp16 vectors) and F4 (its F2 with fp16 vectors).
+    with M), and the depth variants of Table 4: F2 and fp16-F2 (an inner
+    FGMRES(64), fp32 or fp16), F3, fp16-F3 (the inner F8 with fp16 vectors)
+    and F4 (its F2 with fp16 vectors).
     """
     if name == "fp16-F3R":
         p = params()
@@ -132,6 +133,9 @@ def preset(name: str, **kw) -> Params:
         p = params(nlevels=1, m=[64, 0, 0, 0], rich_m=0, m_prec=F64, max_outer=19200)
     elif name == "F2":
         p = params(nlevels=2, m=[100, 64, 0, 0], a_prec=[F64, F32, F32, F32], rich_m=0, m_prec=F16)
+    elif name == "fp16-F2":
+        p = params(nlevels=2, m=[100, 64, 0, 0], a_prec=[F64, F16, F32, F32], v_prec=[F64, F16, F32, F32], rich_m=0,
+                   m_prec=F16)
     elif name == "F3":
         p = params(nlevels=3, m=[100, 8, 8, 0], rich_m=0, m_prec=F16)
     elif name == "fp16-F3":

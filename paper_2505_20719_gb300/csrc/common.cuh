@@ -18,6 +18,8 @@ constexpr int kSlice = 32;           // rows per SELL slice (Sec. 5.2: chunk siz
 constexpr int kMaxInnerM = 15;       // inner FGMRES iterations (fits the fused dot registers)
 constexpr int kMaxDots = kMaxInnerM + 1;
 constexpr int kMaxOuterM = 128;      // outer restart length
+constexpr int kMaxStagedBlocksPerSM = 8;  // blocks per SM of a staged kernel at most (partials sized for it)
+constexpr int kMaxLongM = 64;        // inner levels beyond kMaxInnerM (chunked CGS2, Table 4's F2)
 constexpr int kMaxRich = 8;
 
 typedef __half h16;

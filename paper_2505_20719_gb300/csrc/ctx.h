@@ -184,6 +184,8 @@ bool launch_cgs_fused(Ctx &c, int d, int j, bool last, bool do_norm, cudaStream_
 bool launch_outer_cgs_fused(Ctx &c, cudaStream_t s);
 bool launch_f3_step(Ctx &c, int d, int j, bool last, bool update, cudaStream_t s);
 void launch_combine(Ctx &c, int d, const OutSlot &o, cudaStream_t s);
+// w = A_l Z[j], CGS2 and the Givens step of an inner level with m > kMaxInnerM
+void launch_long_step(Ctx &c, int d, int j, bool last, cudaStream_t s);
 // vround: the output is a level's stored Z[j] rounded to 16 bits (vround_of)
 void launch_M(Ctx &c, int d, int j, const void *in, void *out, int check_depth, bool use_j, cudaStream_t s,
               int vround = 0);

@@ -505,8 +505,8 @@ __global__ void __launch_bounds__(kBlock) k_apply_M(const MS *__restrict__ mv, c
 // ------------------------------------------------------------ outer (fp64) level
 // Reductions with up to kMaxOuterM + 1 sums use partials laid out [d][block]
 // and one warp per sum in the finishing block.
-template <class Fin>
-__device__ __forceinline__ void grid_reduce_many(double *blocksum /*smem, nd*/, int nd, double *partials,
+template <class T, class Fin>
+__device__ __forceinline__ void grid_reduce_many(T *blocksum /*smem, nd*/, int nd, T *partials,
                                                  unsigned *ticket, Fin fin) {
     __shared__ bool am_last;
     for (int d = threadIdx.x; d < nd; d += blockDim.x) partials[(size_t)d * gridDim.x + blockIdx.x] = blocksum[d];
@@ -518,7 +518,7 @@ __device__ __forceinline__ void grid_reduce_many(double *blocksum /*smem, nd*/, 
     __threadfence();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int d = warp; d < nd; d += nwarp) {
-        double s = 0.0;
+        T s = (T)0;
         for (int b = lane; b < (int)gridDim.x; b += 32) s = add_rn(s, __ldcg(partials + (size_t)d * gridDim.x + b));
         s = warp_sum(s);
         if (lane == 0) blocksum[d] = s;
@@ -531,13 +531,13 @@ __device__ __forceinline__ void grid_reduce_many(double *blocksum /*smem, nd*/, 
 }
 
 // block-level sum of `v` into smem slot `dst` (all threads participate)
-__device__ __forceinline__ void block_sum_into(double v, double *dst, double *scratch /*kWarps*/) {
+template <class T> __device__ __forceinline__ void block_sum_into(T v, T *dst, T *scratch /*kWarps*/) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     v = warp_sum(v);
     if (lane == 0) scratch[warp] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = scratch[0];
+        T s = scratch[0];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) s = add_rn(s, scratch[w]);
         *dst = s;
     }
@@ -670,6 +670,141 @@ static __global__ void k_outer_solve_y(LevelDev<double> L) {
         double s = g[r];
         for (int l = r + 1; l < k; ++l) s = fma_rn(-H[r + ldh * l], y[l], s);
         y[r] = div_rn(s, H[r + ldh * r]);
+    }
+}
+
+// ------------------------------------------------ long inner levels (m > kMaxInnerM)
+// An inner FGMRES level with more iterations than the fused dot registers
+// hold (Table 4's F2: an inner FGMRES(64)) runs its CGS2 over the basis in
+// groups of kLongGroup vectors per sweep of 16-byte packs: MODE 0: hA = V^T w;
+// MODE 1: w -= V hA (fma in l order), then hB = V^T w; MODE 2: w -= V h (hB,
+// or hA with one pass), ||w||^2 and max|w| -> Givens step and the child's
+// 16-bit cast scale.  w = A Z[j] comes from the stand-alone SpMV.
+constexpr int kLongGroup = 16;
+constexpr int kLongBlock = 512;
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(kLongBlock) k_long_cgs(LevelDev<T> L, int j, int passes, int last_iter,
+                                                         int want_sigma, T *partials, unsigned *ticket, GridRed<T> gr) {
+    pdl_enter();
+    if (stopped(L.flags, L.depth)) return;
+    constexpr int N = PackN<T>::N;
+    __shared__ T bs[kMaxOuterM + 2];
+    __shared__ T scratch[kLongBlock / 32];
+    __shared__ T hs[kMaxOuterM + 1];
+    const int nv = j + 1;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const int nq = L.n / N;
+    T *__restrict__ w = L.w;
+    const T *__restrict__ V = L.V;
+    const size_t ld = L.ld;
+    T acc2[2] = {(T)0, (T)0};
+    if (MODE >= 1) {
+        const T *h = (MODE == 1 || passes == 1) ? L.hA() : L.hB();
+        for (int l = threadIdx.x; l < nv; l += blockDim.x) hs[l] = h[l];
+        __syncthreads();
+        for (int q = tid; q < nq; q += nth) {
+            Pack<T, N> wv = ldp<T, N>(w + (size_t)q * N);
+            int l = 0;
+            for (; l + 4 <= nv; l += 4) {
+                Pack<T, N> v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = ldp<T, N>(V + (size_t)(l + u) * ld + (size_t)q * N);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-hs[l + u], v[u].v[e], wv.v[e]);
+            }
+            for (; l < nv; ++l) {
+                const Pack<T, N> v = ldp<T, N>(V + (size_t)l * ld + (size_t)q * N);
+#pragma unroll
+                for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-hs[l], v.v[e], wv.v[e]);
+            }
+            stp<T, N>(w + (size_t)q * N, wv);
+            if (MODE == 2) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) {
+                    acc2[0] = fma_rn(wv.v[e], wv.v[e], acc2[0]);
+                    acc2[1] = fmax(acc2[1], fabs(wv.v[e]));
+                }
+            }
+        }
+        for (int i = nq * N + tid; i < L.n; i += nth) {
+            T wi = w[i];
+            for (int l = 0; l < nv; ++l) wi = fma_rn(-hs[l], V[(size_t)l * ld + i], wi);
+            w[i] = wi;
+            if (MODE == 2) {
+                acc2[0] = fma_rn(wi, wi, acc2[0]);
+                acc2[1] = fmax(acc2[1], fabs(wi));
+            }
+        }
+    }
+    if (MODE <= 1) {
+        for (int l0 = 0; l0 < nv; l0 += kLongGroup) {
+            T acc[kLongGroup];
+#pragma unroll
+            for (int g = 0; g < kLongGroup; ++g) acc[g] = (T)0;
+            for (int q = tid; q < nq; q += nth) {
+                const Pack<T, N> wv = ldp<T, N>(w + (size_t)q * N);
+#pragma unroll
+                for (int g = 0; g < kLongGroup; ++g)
+                    if (l0 + g < nv) {
+                        const Pack<T, N> v = ldp<T, N>(V + (size_t)(l0 + g) * ld + (size_t)q * N);
+#pragma unroll
+                        for (int e = 0; e < N; ++e) acc[g] = fma_rn(v.v[e], wv.v[e], acc[g]);
+                    }
+            }
+            for (int i = nq * N + tid; i < L.n; i += nth) {
+                const T wi = w[i];
+#pragma unroll
+                for (int g = 0; g < kLongGroup; ++g)
+                    if (l0 + g < nv) acc[g] = fma_rn(V[(size_t)(l0 + g) * ld + i], wi, acc[g]);
+            }
+#pragma unroll
+            for (int g = 0; g < kLongGroup; ++g)
+                if (l0 + g < nv) block_sum_into(acc[g], &bs[l0 + g], scratch);
+        }
+        grid_reduce_many(bs, nv, partials, ticket, [&](T *res) {
+            T *h = (MODE == 0) ? L.hA() : L.hB();
+            for (int l = 0; l < nv; ++l) h[l] = res[l];
+        });
+    } else {
+        grid_reduce<T, 2>(acc2, 1, true, gr, [&](T *res) {
+            T hcol[kMaxOuterM + 1];
+            const T *hA = L.hA(), *hB = L.hB();
+            for (int l = 0; l < nv; ++l) hcol[l] = (passes == 2) ? add_rn(hA[l], hB[l]) : hA[l];
+            const T hn = sqrt_rn(res[0]);
+            givens_column(L, j, hcol, hn, last_iter != 0);
+            T *ms = L.misc();
+            if (want_sigma && hn > (T)0) {
+                const T sig = pow2_scale_for(mul_rn(res[1], ms[MS_INV]));
+                ms[MS_SIGMA] = sig;
+                ms[MS_INV_SIGMA] = div_rn((T)1, sig);
+            } else {
+                ms[MS_SIGMA] = (T)1;
+                ms[MS_INV_SIGMA] = (T)1;
+            }
+        });
+    }
+}
+
+// z = sum_{k < kdim} y_k Z[k] (fma in k order) into the parent's slot of a
+// long level, times D^-1/2 when returning to level 0 (as k_combine)
+template <class T, class TP>
+__global__ void __launch_bounds__(kVecBlock) k_combine_long(LevelDev<T> L, TP *out, const double *dsc) {
+    pdl_enter();
+    if (stopped(L.flags, L.depth - 1)) return;
+    const int *fl = L.fl();
+    const int k = fl[IF_KDIM];
+    const bool nonfinite = fl[IF_NONFINITE] != 0 && k == 0;
+    __shared__ T ys[kMaxOuterM];
+    for (int l = threadIdx.x; l < k; l += blockDim.x) ys[l] = L.y()[l];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
+        T s = (T)0;
+        for (int l = 0; l < k; ++l) s = fma_rn(ys[l], L.Z[(size_t)l * L.ld + i], s);
+        if (nonfinite) s = (T)NAN;
+        out[i] = dsc ? (TP)mul_rn(dsc[i], (double)s) : (TP)s;
     }
 }
 

@@ -177,7 +177,7 @@ bool outer_dispatch(Ctx &c, cudaStream_t s, bool plan_only) {
 // ---------------------------------------------------------------- whole step
 bool step_eligible(const Ctx &c, int d) {
     const f3r_params &p = c.prm;
-    return p.fuse_cgs && c.coop && d >= 1 && d == p.nlevels - 1 && c.L[d].child == CHILD_R &&
+    return p.fuse_cgs && c.coop && d >= 1 && d == p.nlevels - 1 && c.L[d].child == CHILD_R && c.L[d].m <= kMaxInnerM &&
            c.L[d].v_prec == F3R_F32 && c.L[d].a_prec == F3R_F16 && p.rich_m == 2 && p.rich_v_prec == F3R_F16 &&
            p.rich_a_prec == F3R_F16 && p.m_prec == F3R_F16 && p.precond == F3R_PC_JACOBI && c.a16;
 }
@@ -267,7 +267,8 @@ void plan_cgs_fused(Ctx &c) {
     for (int d = 0; d < 4; ++d) c.fplan[d] = FusedPlan{};
     if (!c.prm.fuse_cgs || !c.coop) return;
     outer_dispatch(c, nullptr, true);
-    for (int d = 1; d < c.prm.nlevels; ++d) fused_dispatch(c, d, 0, false, false, nullptr, true);
+    for (int d = 1; d < c.prm.nlevels; ++d)
+        if (c.L[d].m <= kMaxInnerM) fused_dispatch(c, d, 0, false, false, nullptr, true);
     c.stplan = StepPlan{};
     const int d = c.prm.nlevels - 1;
     if (!c.prm.fuse_step || !step_eligible(c, d)) return;

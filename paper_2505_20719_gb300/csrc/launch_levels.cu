@@ -245,8 +245,14 @@ template <class T, class TP>
 static void comb_go(Ctx &c, int d, const OutSlot &o, cudaStream_t s) {
     prof_begin(c, PK_COMBINE, d, s);
     const int md = maxd_bucket(c.L[d].m);
-    auto kern = (md == 4) ? k_combine<T, TP, 4> : (md == 8) ? k_combine<T, TP, 8> : k_combine<T, TP, 16>;
-    launch_pdl(kern, dim3(c.Gv), dim3(kVecBlock), 0, s, levdev<T>(c, d), (TP *)o.ptr, nullptr, 0, o.dscale ? c.dsc : nullptr);
+    if (c.L[d].m > kMaxInnerM) {
+        launch_pdl(k_combine_long<T, TP>, dim3(c.Gv), dim3(kVecBlock), 0, s, levdev<T>(c, d), (TP *)o.ptr,
+                   o.dscale ? c.dsc : nullptr);
+    } else {
+        auto kern = (md == 4) ? k_combine<T, TP, 4> : (md == 8) ? k_combine<T, TP, 8> : k_combine<T, TP, 16>;
+        launch_pdl(kern, dim3(c.Gv), dim3(kVecBlock), 0, s, levdev<T>(c, d), (TP *)o.ptr, nullptr, 0,
+                   o.dscale ? c.dsc : nullptr);
+    }
     prof_end(c, s);
     c.launches++;
 }
@@ -460,6 +466,45 @@ f3r_status launch_spmv(Ctx &c, int p, int vp, const void *x, void *y, cudaStream
     prof_end(c, s);
     if (st == F3R_OK) c.launches++;
     return st;
+}
+
+// --------------------------------------------------- long inner levels
+// One iteration's w = A_l Z[j] and CGS2 + Givens of a level with m > kMaxInnerM.
+template <class T> static void long_cgs_go(Ctx &c, int d, int j, bool last, cudaStream_t s) {
+    const LevelDev<T> L = levdev<T>(c, d);
+    T *part = (T *)c.partials;
+    const int ws = want_sigma(c, d), passes = c.prm.cgs_passes, li = last ? 1 : 0;
+    // two blocks per SM at most: [vector][block] partials fit the scratch (kMaxLongM + 1 rows)
+    const int g = std::max(1, std::min(ceil_div(c.n / (16 / (int)sizeof(T)), kLongBlock), 2 * c.nsm));
+    launch_pdl(k_long_cgs<T, 0>, dim3(g), dim3(kLongBlock), 0, s, L, j, passes, li, ws, part, c.ticket, gred<T>(c, kMaxDots));
+    if (passes == 2) {
+        launch_pdl(k_long_cgs<T, 1>, dim3(g), dim3(kLongBlock), 0, s, L, j, passes, li, ws, part, c.ticket, gred<T>(c, kMaxDots));
+        c.launches++;
+    }
+    launch_pdl(k_long_cgs<T, 2>, dim3(g), dim3(kLongBlock), 0, s, L, j, passes, li, ws, part, c.ticket, gred<T>(c, kMaxDots));
+    c.launches += 2;
+}
+
+void launch_long_step(Ctx &c, int d, int j, bool last, cudaStream_t s) {
+    const LevelHost &H = c.L[d];
+    const float *rs = c.prm.row_scale ? c.rs : nullptr;
+    const char *z = (const char *)H.Z + (size_t)j * c.ld * level_vec_bytes(c, d);
+    prof_begin(c, PK_SPMV_DOTS, d, s);
+    if (H.v_prec == F3R_F64) {
+        spmv_go<double, double, double>(c, c.ah64, nullptr, (const double *)z, (double *)H.w, s);
+    } else {
+        switch (H.a_prec) {
+            case F3R_F32: spmv_go<float, float, float>(c, c.a32, nullptr, (const float *)z, (float *)H.w, s); break;
+            case F3R_F16: spmv_go<h16, float, float>(c, c.a16, rs, (const float *)z, (float *)H.w, s); break;
+            default: spmv_go<b16, float, float>(c, c.abf, rs, (const float *)z, (float *)H.w, s); break;
+        }
+    }
+    prof_end(c, s);
+    c.launches++;
+    prof_begin(c, PK_CGS_FINAL, d, s);
+    if (H.v_prec == F3R_F64) long_cgs_go<double>(c, d, j, last, s);
+    else long_cgs_go<float>(c, d, j, last, s);
+    prof_end(c, s);
 }
 
 }  // namespace f3r

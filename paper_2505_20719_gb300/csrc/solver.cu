@@ -54,7 +54,7 @@ f3r_status check_params(const f3r_params &p) {
     if (p.m[0] < 1 || p.m[0] > kMaxOuterM) return F3R_ERR_ARG;
     if (p.a_prec[0] != F3R_F64 || p.v_prec[0] != F3R_F64) return F3R_ERR_ARG;
     for (int d = 1; d < p.nlevels; ++d) {
-        if (p.m[d] < 1 || p.m[d] > kMaxInnerM) return F3R_ERR_ARG;
+        if (p.m[d] < 1 || p.m[d] > kMaxLongM) return F3R_ERR_ARG;
         if (p.v_prec[d] == F3R_F64) {
             if (p.a_prec[d] != F3R_F64) return F3R_ERR_UNSUPPORTED;
         } else if (p.v_prec[d] == F3R_F32) {
@@ -142,19 +142,20 @@ long long calls_per_call(const Ctx &c, int d) {
 }
 
 void *zslot(Ctx &c, int d, int j) {
-    return (char *)c.L[d].Z + (size_t)j * c.ld * prec_bytes(c.L[d].v_prec);
+    return (char *)c.L[d].Z + (size_t)j * c.ld * level_vec_bytes(c, d);
 }
 void *vslot(Ctx &c, int d, int j) {
-    return (char *)c.L[d].V + (size_t)j * c.ld * prec_bytes(c.L[d].v_prec);
+    return (char *)c.L[d].V + (size_t)j * c.ld * level_vec_bytes(c, d);
 }
 void *misc_of(Ctx &c, int d) {
-    return (char *)c.L[d].scal + (size_t)scal_misc(c.L[d].m) * prec_bytes(c.L[d].v_prec);
+    return (char *)c.L[d].scal + (size_t)scal_misc(c.L[d].m) * level_vec_bytes(c, d);
 }
 
 // One call of inner FGMRES level d (x0 = 0, m_d iterations, no convergence
 // test), whose normalised input sits in V[0] / its scalars; result to `out`.
 void run_level(Ctx &c, int d, const OutSlot &out, long long &pos, cudaStream_t s) {
     LevelHost &L = c.L[d];
+    const bool lng = L.m > kMaxInnerM;  // Table 4's F2: CGS2 over the basis in chunks
     launch_normalize(c, d, false, 0, s);
     for (int j = 0; j < L.m; ++j) {
         if (L.child == CHILD_F) {
@@ -164,7 +165,7 @@ void run_level(Ctx &c, int d, const OutSlot &out, long long &pos, cudaStream_t s
             run_level(c, d + 1, o, pos, s);
         } else if (L.child == CHILD_R) {
             // the whole iteration in one cooperative launch when it applies
-            if (launch_f3_step(c, d, j, j == L.m - 1, is_update(c, pos), s)) {
+            if (!lng && launch_f3_step(c, d, j, j == L.m - 1, is_update(c, pos), s)) {
                 ++pos;
                 continue;
             }
@@ -172,6 +173,11 @@ void run_level(Ctx &c, int d, const OutSlot &out, long long &pos, cudaStream_t s
             ++pos;
         } else {
             launch_M(c, d, j, vslot(c, d, j), zslot(c, d, j), d, false, s, vround_of(c, d));
+        }
+        if (lng) {
+            launch_long_step(c, d, j, j == L.m - 1, s);
+            if (j < L.m - 1) launch_normalize(c, d, true, j + 1, s);
+            continue;
         }
         launch_spmv_dots(c, d, j, s);
         if (launch_cgs_fused(c, d, j, j == L.m - 1, j < L.m - 1, s)) continue;
@@ -435,11 +441,12 @@ f3r_status f3r_setup(f3r_ctx **out, int32_t n, int64_t nnz, const int32_t *rowpt
     c.apply_misc = dalloc(c, sizeof(double) * MS_COUNT);
     // partial sums: grid reductions, the outer CGS, and the fused kernels'
     // [vector][block] regions (two of kMaxOuterM + 1 rows, one more row; <= 2 blocks per SM)
-    const size_t pbytes = std::max({(size_t)c.nsm * 8 * kMaxDots * sizeof(double),
+    const size_t pbytes = std::max({(size_t)c.nsm * kMaxStagedBlocksPerSM * kMaxDots * sizeof(double),
                                     (size_t)(kMaxOuterM + 2) * c.G1 * sizeof(double),
-                                    (size_t)(2 * (kMaxOuterM + 1) + 2) * c.nsm * 2 * sizeof(double)});
+                                    (size_t)(2 * (kMaxOuterM + 1) + 2) * c.nsm * 2 * sizeof(double),
+                                    (size_t)(kMaxLongM + 1) * c.nsm * 2 * sizeof(double)});
     c.partials = dalloc(c, pbytes);
-    c.hpart = dalloc(c, (size_t)c.nsm * 8 * kMaxDots * sizeof(double));
+    c.hpart = dalloc(c, (size_t)c.nsm * kMaxStagedBlocksPerSM * kMaxDots * sizeof(double));
     c.ticket = (unsigned *)dalloc(c, sizeof(unsigned) * 4);
     c.coop = (unsigned *)dalloc(c, sizeof(unsigned) * 4);
     c.err = (int *)dalloc(c, sizeof(int) * 4);

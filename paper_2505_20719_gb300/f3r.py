@@ -182,8 +182,8 @@ def default_params(**kw) -> Params:
 def preset(name: str, **kw) -> Params:
     """Named configurations: fp16-F3R (Table 1), bf16-F3R (bf16 inner storage
     with per-row scaling), fp32-F3R and fp64-F3R (Sec. 5), fgmres64 (fp64
-    restarted FGMRES(64) with M, Sec. 5), and the depth variants F3, fp16-F3
-    and F4 of Table 4.  Their fp16-vector levels compute in fp32 and round
+    restarted FGMRES(64) with M, Sec. 5), and the depth variants F2, fp16-F2,
+    F3, fp16-F3 and F4 of Table 4.  Their fp16-vector levels compute in fp32 and round
     every stored V and Z value to fp16 (held in fp32 arrays)."""
     if name == "fp16-F3R":
         p = default_params()
@@ -197,6 +197,13 @@ def preset(name: str, **kw) -> Params:
                            rich_v_prec=F64, m_prec=F64)
     elif name == "fgmres64":
         p = default_params(nlevels=1, m=[64, 0, 0, 0], rich_m=0, m_prec=F64, max_outer=19200)
+    elif name == "F2":
+        # Table 4: (F100, F64, M), the inner FGMRES(64) in fp32
+        p = default_params(nlevels=2, m=[100, 64, 0, 0], a_prec=[F64, F32, F32, F32], rich_m=0, m_prec=F16)
+    elif name == "fp16-F2":
+        # Table 4: the inner FGMRES(64) with fp16 A and fp16 vectors
+        p = default_params(nlevels=2, m=[100, 64, 0, 0], a_prec=[F64, F16, F32, F32], v_prec=[F64, F16, F32, F32],
+                           rich_m=0, m_prec=F16)
     elif name == "F3":
         # Table 4: (F100, F8, F8, M), the inner F8 with fp16 A and fp32 vectors
         p = default_params(nlevels=3, m=[100, 8, 8, 0], rich_m=0, m_prec=F16)

@@ -1,5 +1,6 @@
-"""fp16-vector FGMRES levels (Table 4: fp16-F3's inner F8, F4's F2) on the GPU
-against the oracle's same configuration.
+"""fp16-vector FGMRES levels (Table 4: fp16-F3's inner F8, F4's F2, fp16-F2's
+inner FGMRES(64)) and the fp32 inner FGMRES(64) of F2 on the GPU against the
+oracle's same configuration.
 
 The level computes in fp32 and rounds every stored V and Z value to fp16
 (held in fp32 arrays).  Checked: each basis vector the GPU stored is a vector
@@ -25,7 +26,8 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2505_20719_gb300 import f3r  # noqa: E402
 
 U16 = 2.0 ** -11
-_LEVELS = [("fp16-F3", 2), ("F4", 3)]
+_LEVELS = [("fp16-F3", 2), ("F4", 3), ("fp16-F2", 1)]
+_IDS = ["fp16-F3 F8", "F4 F2", "fp16-F2 F64"]
 
 
 def dev(a):
@@ -40,7 +42,7 @@ def system(request):
     return prob, request.param, v
 
 
-@pytest.mark.parametrize("preset,level", _LEVELS, ids=["fp16-F3 F8", "F4 F2"])
+@pytest.mark.parametrize("preset,level", _LEVELS, ids=_IDS)
 def test_fp16_level_call_matches_oracle(system, preset, level):
     prob, ds, v = system
     P = O.Problem(prob, diag_scale=ds)
@@ -60,7 +62,7 @@ def test_fp16_level_call_matches_oracle(system, preset, level):
     assert err <= 2 * U16 and emax <= 8 * U16
     assert e64 <= 20 * U16
     m = f3r.preset(preset).m[level]
-    for k in range(m + 1):
+    for k in range(m):  # an inner level never forms V[m]
         out = torch.empty(prob.n, dtype=torch.float32, device="cuda")
         s.get_basis(level, k, out)
         vk = out.cpu().numpy()
@@ -81,4 +83,21 @@ def test_fp32_level_basis_is_not_fp16(system):
     torch.cuda.synchronize()
     vk = out.cpu().numpy()
     assert not np.array_equal(vk, vk.astype(np.float16).astype(np.float32))
+    s.close()
+
+
+def test_long_fp32_level_call_matches_oracle(system):
+    """F2's inner FGMRES(64) (chunked CGS2 beyond the fused register path) in
+    fp32 against the oracle's call, to 1e-4 of the norm (64 fp32 iterations)."""
+    prob, ds, v = system
+    P = O.Problem(prob, diag_scale=ds)
+    zo = P.apply(O.preset("F2", diag_scale=ds), O.rich_state(), 1, v)
+    s = f3r.Solver(dev(prob.rowptr), dev(prob.colidx), dev(prob.val), f3r.preset("F2", diag_scale=ds))
+    z = torch.empty(prob.n, dtype=torch.float32, device="cuda")
+    s.apply(1, dev(v.astype(np.float32)), z)
+    torch.cuda.synchronize()
+    zg = z.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(zg - zo) / np.linalg.norm(zo)
+    print(f"F2 level 1 ds={ds}: |z - z_oracle|/|z| = {err:.3e}")
+    assert err <= 1e-4
     s.close()

@@ -284,11 +284,12 @@ def test_solve_convdiff_matches_oracle(kind):
     _check_history(res, ref, prob, xg)
 
 
-@pytest.mark.parametrize("name", ["F3", "fp16-F3", "F4"])
+@pytest.mark.parametrize("name", ["F2", "fp16-F2", "F3", "fp16-F3", "F4"])
 def test_depth_variants_match_oracle(name):
-    """The depth variants of Table 4 (F3: (F100, F8, F8, M); fp16-F3: its
-    inner F8 with fp16 vectors; F4: (F100, F8, F4, F2, M), the F2 with fp16
-    vectors) against the oracle's same configurations."""
+    """The depth variants of Table 4 (F2: (F100, F64, M) in fp32, fp16-F2 its
+    fp16 version; F3: (F100, F8, F8, M); fp16-F3: its inner F8 with fp16
+    vectors; F4: (F100, F8, F4, F2, M), the F2 with fp16 vectors) against the
+    oracle's same configurations."""
     prob = G.diffusion3d_7pt(dims=(24, 24, 24), seed=102)
     s = solver(prob, f3r.preset(name))
     x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")

@@ -76,6 +76,29 @@ def test_inner_arnoldi_relation_fp32(orc, case, level, aprec):
     assert np.all(np.diag(H, -1)[:k] > 0)   # h_{j+1,j} = ||w|| > 0
 
 
+@pytest.mark.parametrize("case", _CASES, ids=[c[0] for c in _CASES])
+def test_long_inner_level_arnoldi_relation(orc, case):
+    """Table 4's F2: an inner fp32 FGMRES(64) keeps the Arnoldi relation and
+    an orthonormal basis to 50 m u32, and its output is Z y for the numpy
+    least-squares y of the recorded Hessenberg matrix."""
+    prob = case[1]()
+    P = O.Problem(prob)
+    prm = O.preset("F2")
+    v = rng.normal(45, 1, prob.n).astype(np.float32).astype(np.float64)
+    z, V, Z, H, g, k = P.inner_arnoldi(prm, O.rich_state(), 1, v)
+    m = prm.m[1]
+    assert m == 64 and k == m
+    A = _level_matrix(P, prob, O.F32)
+    R = A @ Z[:k].T - V[:k + 1].T @ H[:k + 1, :k]
+    col = np.linalg.norm(R, axis=0) / (sp.linalg.norm(A) * np.linalg.norm(Z[:k], axis=1))
+    assert col.max() <= 50 * m * U32
+    assert np.abs(V[:k + 1] @ V[:k + 1].T - np.eye(k + 1)).max() <= 50 * m * U32
+    e1 = np.zeros(k + 1)
+    e1[0] = np.linalg.norm(v)
+    y, *_ = np.linalg.lstsq(H[:k + 1, :k], e1, rcond=None)
+    assert np.linalg.norm(z - Z[:k].T @ y) <= 1e-4 * np.linalg.norm(z)
+
+
 def test_inner_orthogonality_pin_rejects_single_pass(orc):
     """The orthogonality bound separates CGS2 from one classical pass: with one
     pass the fp32 F_{m2} basis loses orthogonality by orders of magnitude."""
