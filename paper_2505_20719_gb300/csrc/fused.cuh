@@ -364,6 +364,7 @@ __global__ void __launch_bounds__(kFusedThreads, (MAXD <= 8 && kFusedThreads <= 
 // [vector][block]; phase-0 and phase-1 partials use separate regions so that a
 // block still reading one never races a block writing the next.
 constexpr int kOuterGroup = 8;
+constexpr int kOuterUnroll = 4;  // 16-byte packs per thread in flight in the outer sweeps
 
 template <class TC, int CHILD>
 __global__ void __launch_bounds__(kFusedThreads, kFusedThreads <= 512 ? 2 : 1)
@@ -389,26 +390,39 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedThreads <= 512 ? 2 : 1)
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) ws[i] = L.w[r0 + i];
     __syncthreads();
 
+    // The block's rows of each basis vector are streamed one vector at a time
+    // (one contiguous run per block in flight, kOuterUnroll packs per thread),
+    // with the same fma order per sum and per element as a row-major sweep.
     // dots V[0..nv)^T ws into part[l * G + block]
     auto dots = [&](double *part) {
         for (int l0 = 0; l0 < nv; l0 += kOuterGroup) {
             double acc[kOuterGroup];
 #pragma unroll
             for (int k = 0; k < kOuterGroup; ++k) acc[k] = 0.0;
-            for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-                const Pack<double, N> wv = ldp<double, N>(ws + (size_t)q * N);
 #pragma unroll
-                for (int k = 0; k < kOuterGroup; ++k)
-                    if (l0 + k < nv) {
-                        const Pack<double, N> v = ldp<double, N>(V + (size_t)(l0 + k) * L.ld + (size_t)q * N);
+            for (int k = 0; k < kOuterGroup; ++k) {
+                if (l0 + k < nv) {
+                    const double *__restrict__ Vl = V + (size_t)(l0 + k) * L.ld;
+                    for (int q0 = threadIdx.x; q0 < nq; q0 += blockDim.x * kOuterUnroll) {
+                        Pack<double, N> v[kOuterUnroll];
 #pragma unroll
-                        for (int e = 0; e < N; ++e) acc[k] = fma_rn(v.v[e], wv.v[e], acc[k]);
+                        for (int u = 0; u < kOuterUnroll; ++u) {
+                            const int q = q0 + u * (int)blockDim.x;
+                            if (q < nq) v[u] = ldp<double, N>(Vl + (size_t)q * N);
+                        }
+#pragma unroll
+                        for (int u = 0; u < kOuterUnroll; ++u) {
+                            const int q = q0 + u * (int)blockDim.x;
+                            if (q < nq) {
+                                const Pack<double, N> wv = ldp<double, N>(ws + (size_t)q * N);
+#pragma unroll
+                                for (int e = 0; e < N; ++e) acc[k] = fma_rn(v[u].v[e], wv.v[e], acc[k]);
+                            }
+                        }
                     }
+                    for (int i = nq * N + threadIdx.x; i < cnt; i += blockDim.x) acc[k] = fma_rn(Vl[i], ws[i], acc[k]);
+                }
             }
-            for (int i = nq * N + threadIdx.x; i < cnt; i += blockDim.x)
-#pragma unroll
-                for (int k = 0; k < kOuterGroup; ++k)
-                    if (l0 + k < nv) acc[k] = fma_rn(V[(size_t)(l0 + k) * L.ld + i], ws[i], acc[k]);
             block_reduce<double, kOuterGroup>(acc, min(kOuterGroup, nv - l0), false, tot);
             if (threadIdx.x < kOuterGroup && l0 + (int)threadIdx.x < nv)
                 part[(size_t)(l0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
@@ -426,21 +440,31 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedThreads <= 512 ? 2 : 1)
         }
         __syncthreads();
     };
-    // ws -= V hs (row sweep)
+    // ws -= V hs (fma in l order per element; a thread owns the same
+    // positions of ws for every l)
     auto update = [&]() {
-        for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-            Pack<double, N> wv = ldp<double, N>(ws + (size_t)q * N);
-            for (int l = 0; l < nv; ++l) {
-                const Pack<double, N> v = ldp<double, N>(V + (size_t)l * L.ld + (size_t)q * N);
+        for (int l = 0; l < nv; ++l) {
+            const double h = hs[l];
+            const double *__restrict__ Vl = V + (size_t)l * L.ld;
+            for (int q0 = threadIdx.x; q0 < nq; q0 += blockDim.x * kOuterUnroll) {
+                Pack<double, N> v[kOuterUnroll];
 #pragma unroll
-                for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-hs[l], v.v[e], wv.v[e]);
+                for (int u = 0; u < kOuterUnroll; ++u) {
+                    const int q = q0 + u * (int)blockDim.x;
+                    if (q < nq) v[u] = ldp<double, N>(Vl + (size_t)q * N);
+                }
+#pragma unroll
+                for (int u = 0; u < kOuterUnroll; ++u) {
+                    const int q = q0 + u * (int)blockDim.x;
+                    if (q < nq) {
+                        Pack<double, N> wv = ldp<double, N>(ws + (size_t)q * N);
+#pragma unroll
+                        for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-h, v[u].v[e], wv.v[e]);
+                        stp<double, N>(ws + (size_t)q * N, wv);
+                    }
+                }
             }
-            stp<double, N>(ws + (size_t)q * N, wv);
-        }
-        for (int i = nq * N + threadIdx.x; i < cnt; i += blockDim.x) {
-            double wi = ws[i];
-            for (int l = 0; l < nv; ++l) wi = fma_rn(-hs[l], V[(size_t)l * L.ld + i], wi);
-            ws[i] = wi;
+            for (int i = nq * N + threadIdx.x; i < cnt; i += blockDim.x) ws[i] = fma_rn(-h, Vl[i], ws[i]);
         }
         __syncthreads();
     };

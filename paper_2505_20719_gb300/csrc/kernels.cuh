@@ -706,12 +706,12 @@ __global__ void __launch_bounds__(kLongBlock) k_long_cgs(LevelDev<T> L, int j, i
         for (int q = tid; q < nq; q += nth) {
             Pack<T, N> wv = ldp<T, N>(w + (size_t)q * N);
             int l = 0;
-            for (; l + 4 <= nv; l += 4) {
-                Pack<T, N> v[4];
+            for (; l + 8 <= nv; l += 8) {
+                Pack<T, N> v[8];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = ldp<T, N>(V + (size_t)(l + u) * ld + (size_t)q * N);
+                for (int u = 0; u < 8; ++u) v[u] = ldp<T, N>(V + (size_t)(l + u) * ld + (size_t)q * N);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 8; ++u)
 #pragma unroll
                     for (int e = 0; e < N; ++e) wv.v[e] = fma_rn(-hs[l + u], v[u].v[e], wv.v[e]);
             }
