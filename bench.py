@@ -247,7 +247,7 @@ def run_batched(args):
         for r in range(B.shape[0]):
             Bs.append(T(B[r]))
             Xs.append(torch.zeros(p.n, dtype=torch.float64, device=dev))
-    bs = f3r.BatchedSolver(systems, f3r.default_params())
+    bs = f3r.BatchedSolver(systems, f3r.default_params(batch_wide=args.batch_wide))
     chosen = bs.autotune(Bs, Xs)
     times = []
     for it in range(args.warmup + args.steps):
@@ -285,8 +285,9 @@ def run_batched(args):
     # time of each path: the persistent launch (one graph; every instance in it
     # reports the launch's time) and the large systems' instances solved one
     # after another on the whole GPU
-    launch_ms = next((r.t_solve_ms for r in res if r.path == 0), 0.0)
+    launch_ms = next((r.t_solve_ms for r in res if r.path in (0, 2)), 0.0)
     single_ms = sum(r.t_solve_ms for r in res if r.path == 1)
+    wi = bs.wide_info()
     out = {"metric": "batched F3R throughput (systems x right-hand sides solved to 1e-9 per second)",
            "value": ninst / (ms / 1e3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "data": "synthetic",
@@ -295,11 +296,16 @@ def run_batched(args):
                       "shape": {"cluster": info["cluster"], "threads_per_block": info["threads"],
                                 "blocks": info["grid"], "chosen_by": "f3r_batched_autotune"}},
            "paths": {"persistent_launch": {"instances": info["instances_launch"], "rows": info["rows_launch"],
-                                           "ms": launch_ms, "graph_launches": info["graph_launches"]},
+                                           "ms": launch_ms, "graph_launches": info["graph_launches"],
+                                           "wide_teams": {"clusters_per_team": wi["clusters_per_team"],
+                                                          "teams": wi["teams"], "instances": wi["instances"],
+                                                          "rows": wi["rows"],
+                                                          "note": "instances of systems of at least batch_split "
+                                                                  "rows (2048 per SM), each on a team of clusters"}},
                      "single_system": {"instances": info["instances_single"], "rows": info["rows_single"],
                                        "ms": single_ms,
-                                       "note": "systems of at least batch_split rows (2048 per SM), solved "
-                                               "one after another on the whole GPU before the launch"}},
+                                       "note": "with --batch-wide < 0: the large systems one after another on "
+                                               "the whole GPU before the launch"}},
            "converged": ok, "max_outer_iters": max(r.outer_iters for r in res),
            "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
            "device_bytes": bs.device_bytes}
@@ -502,6 +508,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diffusion7_128", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch-wide", type=int, default=0,
+                    help="batched64: clusters per wide team for the large systems (0 automatic; < 0 the "
+                         "single-system path)")
     ap.add_argument("--kind", default="fp16-F3R")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")

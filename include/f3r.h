@@ -100,11 +100,15 @@ typedef struct {
                            cooperative launch when the default precision schedule, Jacobi M
                            and m4 = 2 apply; 0 (default): separate launches, which measured
                            as fast inside CUDA graphs with more blocks per SM */
-    int batch_split;    /* f3r_setup_batched only: systems of at least this many rows are solved
-                           one after another by the single-system path (the whole GPU each),
-                           the others in the one persistent launch; 0 (default): 2048 rows per
-                           SM of the device; < 0: every system in the persistent launch */
-    int reserved[2];
+    int batch_split;    /* f3r_setup_batched only: systems of at least this many rows are large
+                           (see batch_wide); 0 (default): 2048 rows per SM of the device; < 0: no
+                           system is large */
+    int batch_wide;     /* f3r_setup_batched only: the large systems' instances run in the same
+                           persistent launch, each on a wide team of this many thread-block
+                           clusters (0, default: an eighth of the launch's clusters, at least 2);
+                           < 0: they are solved one after another by the single-system path
+                           (the whole GPU each) before the launch */
+    int reserved;
 } f3r_params;
 
 typedef struct {
@@ -278,10 +282,17 @@ f3r_status f3r_solve_krylov(f3r_ctx *ctx, int method, const double *b, double *x
  * FGMRES(m1) with its convergence test and restarts, fp32 FGMRES(m2),
  * FGMRES(m3) with fp16 A, fp16 Richardson R_2 with adaptive weights
  * (Algorithm 1), Jacobi M.  Clusters take instances largest-first from an
- * atomic work queue.  Systems of at least params.batch_split rows are set up
- * as single-system contexts and their instances solved one after another
- * (the whole GPU each) before the persistent launch: on one cluster they
- * would keep the launch waiting long after the other clusters finished. */
+ * atomic work queue.  An instance of a large system (params.batch_split rows
+ * or more) is solved in the same launch by a wide team of several clusters
+ * that meet at bounded barriers in global memory (on one cluster it would
+ * keep the launch waiting long after the other clusters finished); the wide
+ * teams take the large instances first, then their clusters join the queue
+ * of the others.  With params.batch_wide < 0 the large systems are set up as
+ * single-system contexts instead and solved one after another (the whole GPU
+ * each) before the launch.  Every cluster of the launch is resident at once
+ * (the grid is the device's cluster occupancy); a wide barrier that waits
+ * longer than ~4 s gives up, and the wide instances then report
+ * F3R_ERR_TIMEOUT. */
 typedef struct f3r_batch f3r_batch;
 
 typedef struct {
@@ -303,7 +314,8 @@ typedef struct {
     double t_solve_ms;       /* device time of the whole persistent launch, or of the
                                 instance's own solve (systems of >= batch_split rows) */
     int system, rhs;         /* which instance */
-    int path;                /* 0: the persistent launch; 1: the single-system path */
+    int path;                /* 0: the persistent launch, one cluster; 1: the single-system
+                                path; 2: the persistent launch, a wide team of clusters */
 } f3r_batch_result;
 
 /* Set up all systems (setup of each matrix as in f3r_setup) and the
@@ -316,9 +328,9 @@ f3r_status f3r_setup_batched(f3r_batch **batch, int nsys, const f3r_system_desc 
 
 /* Solve every instance: B[q] and X[q] are device pointers (n of system q's
  * system fp64 values) for instance q, instances numbered system by system
- * and right-hand side by right-hand side; X[q] holds x0 on entry.  The
- * instances of large systems first (f3r_solve each), then one persistent
- * kernel launch for the rest, replayed as a CUDA graph (the instances' b and x
+ * and right-hand side by right-hand side; X[q] holds x0 on entry.  With
+ * batch_wide < 0 the instances of large systems first (f3r_solve each); one
+ * persistent kernel launch for all the others, replayed as a CUDA graph (the instances' b and x
  * pointers reach it through a pinned host table that the graph copies to the
  * device; one graph per cluster and block size, captured on first use, so the
  * first call should come before any stream capture of the caller's); res
@@ -346,6 +358,10 @@ int f3r_batched_instances(const f3r_batch *batch);
  * by the single-system path (systems of >= batch_split rows), [4] / [5] their
  * rows in all, [6] blocks of the persistent launch, [7] graph launches so far. */
 f3r_status f3r_batched_info(const f3r_batch *batch, int64_t *out);
+/* The wide teams of the last persistent launch, out[4]: [0] clusters per wide
+ * team, [1] wide teams, [2] instances of large systems in the launch, [3]
+ * their rows in all. */
+f3r_status f3r_batched_wide_info(const f3r_batch *batch, int64_t *out);
 int64_t f3r_batched_device_bytes(const f3r_batch *batch);
 void f3r_destroy_batched(f3r_batch *batch);
 

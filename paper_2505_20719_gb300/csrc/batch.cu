@@ -36,6 +36,7 @@ constexpr int kBT = 512;          // threads per block at most (256 or 512, chos
 constexpr int kBW = kBT / 32;     // warps per block at most
 constexpr int kMaxCluster = 8;
 constexpr int kRedMax = 16;       // sums per team reduction
+constexpr int kMaxClustersPerSM = 4;  // clusters of a launch per SM at most (2048 threads per SM)
 
 struct Sys {
     int n, nslices;
@@ -93,13 +94,68 @@ struct Shared {
     int o_stop, o_kdim, o_nonfinite, inst;
 };
 
+// A team solves one instance: one cluster, or (a wide team, for the large
+// systems) k clusters that meet at a barrier in global memory.  rank / size
+// count the team's blocks (cluster kidx holds ranks kidx * csize ..), crank /
+// csize the blocks of this cluster.
 struct Team {
     unsigned rank, size;
+    unsigned crank, csize;
+    int k, kidx;
     int tid, nthr, wid, nwarps, lane;
+    unsigned *bar;   // wide teams: [0] arrivals, [1] generation
+    double *part;    // wide teams: [2][k][kRedMax] cluster sums of the reductions
+    double *dec;     // wide teams: decisions of the team's rank 0 ([0..7]) and the instance ([8])
+    int *abort;      // set when a wide barrier gave up; later wide barriers do not wait
 };
 
-__device__ __forceinline__ void team_sync() {
+constexpr long long kWideWaitCycles = 8000000000LL;  // ~4 s at the 2.07 GHz SM clock
+
+__device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The k clusters of a wide team meet (one thread of each, after its cluster
+// barrier): arrivals counted in bar[0], the last arriver resets it and
+// advances the generation bar[1] the others poll.  The wait is bounded: on
+// giving up it sets *abort, and no later wide barrier waits (the launch then
+// ends with unreliable results for the wide instances, reported as
+// F3R_ERR_TIMEOUT, instead of hanging).
+__device__ void wide_barrier(const Team &tm) {
+    unsigned *cnt = tm.bar, *gen = tm.bar + 1;
+    const unsigned g = ld_acquire_gpu(gen);
+    __threadfence();  // this cluster's writes (ordered by its cluster barrier) before the arrival
+    if (atomicAdd(cnt, 1u) == (unsigned)tm.k - 1) {
+        atomicExch(cnt, 0u);
+        __threadfence();
+        atomicAdd(gen, 1u);
+    } else {
+        const long long t0 = clock64();
+        while (ld_acquire_gpu(gen) == g) {
+            if (*(volatile int *)tm.abort) break;
+            if (clock64() - t0 > kWideWaitCycles) {
+                atomicExch(tm.abort, 1);
+                break;
+            }
+            __nanosleep(100);
+        }
+    }
+    __threadfence();
+}
+
+// barrier of the whole team
+__device__ __forceinline__ void team_sync(const Team &tm) {
+    cluster_sync();
+    if (tm.k > 1) {
+        if (tm.crank == 0 && threadIdx.x == 0) wide_barrier(tm);
+        cluster_sync();
+    }
 }
 
 template <class T> __device__ __forceinline__ T ldcg(const T *p) { return __ldcg(p); }
@@ -134,16 +190,32 @@ __device__ void team_reduce(const Team &tm, Shared &sh, T *acc, int nd, T *out, 
         for (int w = 1; w < nw; ++w) s = mx ? fmax(s, (T)sh.wred[d][w]) : add_rn(s, (T)sh.wred[d][w]);
         sh.red_blk[buf][d] = (double)s;
     }
-    team_sync();
+    cluster_sync();
     if (threadIdx.x < nd) {
         const int d = threadIdx.x;
         const bool mx = is_max && is_max[d];
         T s = (T)0;
-        for (unsigned r = 0; r < tm.size; ++r) {
+        for (unsigned r = 0; r < tm.csize; ++r) {
             const double *rb = cl.map_shared_rank(&sh.red_blk[buf][0], r);
             s = (r == 0) ? (T)rb[d] : (mx ? fmax(s, (T)rb[d]) : add_rn(s, (T)rb[d]));
         }
         sh.red_res[d] = (double)s;
+    }
+    if (tm.k > 1) {
+        // the cluster sums through global memory, summed in cluster order by every block
+        double *pb = tm.part + (size_t)buf * tm.k * kRedMax;
+        if (tm.crank == 0 && threadIdx.x < nd) pb[(size_t)tm.kidx * kRedMax + threadIdx.x] = sh.red_res[threadIdx.x];
+        team_sync(tm);
+        if (threadIdx.x < nd) {
+            const int d = threadIdx.x;
+            const bool mx = is_max && is_max[d];
+            T s = (T)0;
+            for (int c = 0; c < tm.k; ++c) {
+                const T v = (T)__ldcg(pb + (size_t)c * kRedMax + d);
+                s = (c == 0) ? v : (mx ? fmax(s, v) : add_rn(s, v));
+            }
+            sh.red_res[d] = (double)s;
+        }
     }
     __syncthreads();
     for (int d = 0; d < nd; ++d) out[d] = (T)sh.red_res[d];
@@ -305,7 +377,7 @@ __device__ void rich_call(Ctx2 &C, float inv_sigma, float *out) {
                     const int i = s * kSlice + tm.lane;
                     if (i < n) I.rr[i] = Store<h16>::from(sub_rn(to_c<float>(ldcg(I.rin + i)), acc));
                 }
-                team_sync();
+                team_sync(tm);
             }
             float acc[2] = {0.0f, 0.0f};
             for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
@@ -335,7 +407,7 @@ __device__ void rich_call(Ctx2 &C, float inv_sigma, float *out) {
                 if (k == 1) out[i] = mul_rn(z, inv_sigma);
                 else I.rz[i] = Store<h16>::from(z);
             }
-            team_sync();
+            team_sync(tm);
         }
         C.o.m_applies += 2;
     }
@@ -391,14 +463,14 @@ __device__ void inner_level(Ctx2 &C, float *V, float *Z, float *w, LS &L, int m,
             }
             __syncthreads();
         } else {
-            team_sync();
+            team_sync(tm);
         }
     }
     for (int j = 0; j < m && !L.stop; ++j) {
         // child -> Z[j]
         if (LEVEL == 2) inner_level<3>(C, I.V3, I.Z3, I.w3, sh.ls3, C.P.m3, Z + (size_t)j * ld, nullptr);
         else rich_call(C, L.inv_sigma, Z + (size_t)j * ld);
-        team_sync();
+        team_sync(tm);
         // w = A Z[j], hA = V^T w
         const float *zj = Z + (size_t)j * ld;
         float acc[kRedMax];
@@ -488,7 +560,7 @@ __device__ void inner_level(Ctx2 &C, float *V, float *Z, float *w, LS &L, int m,
             }
             __syncthreads();
         } else {
-            team_sync();
+            team_sync(tm);
         }
     }
     // out = sum_k y_k Z[k]
@@ -588,14 +660,14 @@ __device__ void solve_instance(const Team &tm, Shared &sh, const Sys &S, const I
             // Z1[j] = D^-1/2 F2(D^-1/2 V1[j])
             double *zj = I.Z1 + (size_t)j * ld;
             inner_level<2>(C, I.V2, I.Z2, I.w2, sh.ls2, P.m2, nullptr, zj);
-            team_sync();
+            team_sync(tm);
             // w = A Z1[j]; CGS2 against V1[0..j] in chunks of kRedMax
             for (int s = tm.wid; s < S.nslices; s += tm.nwarps) {
                 const double yv = row_sum<double>(S, S.a64, s, tm.lane, [&](int c) { return ldcg(zj + c); });
                 const int i = s * kSlice + tm.lane;
                 if (i < n) I.w1[i] = yv;
             }
-            team_sync();
+            team_sync(tm);
             double hsum[kMaxOuterM + 1];
             for (int p = 0; p < P.cgs_passes; ++p) {
                 double h[kMaxOuterM + 1];
@@ -615,7 +687,7 @@ __device__ void solve_instance(const Team &tm, Shared &sh, const Sys &S, const I
                     I.w1[i] = wi;
                 }
                 for (int l = 0; l <= j; ++l) hsum[l] = (p == 0) ? h[l] : add_rn(hsum[l], h[l]);
-                team_sync();
+                team_sync(tm);
             }
             double an[1] = {0.0};
             for (int i = tm.tid; i < n; i += tm.nthr) {
@@ -656,12 +728,32 @@ __device__ void solve_instance(const Team &tm, Shared &sh, const Sys &S, const I
                 sh.o_stop = (!ok || !(hn > 0.0)) ? 1 : 0;
                 sh.o_inv = (ok && hn > 0.0) ? div_rn(1.0, hn) : 0.0;
                 sh.o_est = div_rn(fabs(g[sh.o_kdim]), nb);
+                if (tm.k > 1) {  // the other clusters of a wide team read them from global memory
+                    tm.dec[0] = (double)sh.o_kdim;
+                    tm.dec[1] = (double)sh.o_stop;
+                    tm.dec[2] = (double)sh.o_nonfinite;
+                    tm.dec[3] = sh.o_est;
+                    tm.dec[4] = sh.o_inv;
+                }
             }
-            team_sync();
-            const Shared *s0 = cl.map_shared_rank(&sh, 0);
-            const int o_kdim = s0->o_kdim, o_stop = s0->o_stop, o_nf = s0->o_nonfinite;
-            const double o_est = s0->o_est, o_inv = s0->o_inv;
-            team_sync();
+            team_sync(tm);
+            int o_kdim, o_stop, o_nf;
+            double o_est, o_inv;
+            if (tm.k > 1) {
+                o_kdim = (int)__ldcg(tm.dec + 0);
+                o_stop = (int)__ldcg(tm.dec + 1);
+                o_nf = (int)__ldcg(tm.dec + 2);
+                o_est = __ldcg(tm.dec + 3);
+                o_inv = __ldcg(tm.dec + 4);
+            } else {
+                const Shared *s0 = cl.map_shared_rank(&sh, 0);
+                o_kdim = s0->o_kdim;
+                o_stop = s0->o_stop;
+                o_nf = s0->o_nonfinite;
+                o_est = s0->o_est;
+                o_inv = s0->o_inv;
+            }
+            team_sync(tm);
             kdim = o_kdim;
             if (o_nf) {
                 nonfinite = true;
@@ -679,13 +771,13 @@ __device__ void solve_instance(const Team &tm, Shared &sh, const Sys &S, const I
                 y[r] = div_rn(s, H[r + ldh * r]);
             }
         }
-        team_sync();
+        team_sync(tm);
         for (int i = tm.tid; i < n; i += tm.nthr) {
             double s = 0.0;
             for (int l = 0; l < kdim; ++l) s = fma_rn(ldcg(y + l), ldcg(I.Z1 + (size_t)l * ld + i), s);
             I.x[i] = add_rn(ldcg(I.x + i), s);
         }
-        team_sync();
+        team_sync(tm);
         if (nonfinite) {
             o.status = F3R_ERR_NONFINITE;
             break;
@@ -695,25 +787,64 @@ __device__ void solve_instance(const Team &tm, Shared &sh, const Sys &S, const I
     o.restarts = cycles > 0 ? cycles - 1 : 0;
 }
 
-__global__ void __launch_bounds__(kBT) k_batch(const Sys *sys, const Inst *inst, const int *order, int ninst, BP P,
-                                               int *queue, Out *outs) {
+// One persistent launch over every instance.  Clusters [0, nteams * kw)
+// first form nteams wide teams of kw clusters that take the large systems'
+// instances (worder, largest first) from queue[1]; then every cluster, alone,
+// takes the other instances (order) from queue[0].
+__global__ void __launch_bounds__(kBT) k_batch(const Sys *sys, const Inst *inst, const int *order, int ninst,
+                                               const int *worder, int nwide, int kw, int nteams, BP P, int *queue,
+                                               unsigned *wbar, double *wpart, double *wdec, int *abort, Out *outs) {
     __shared__ Shared sh;
     cg::cluster_group cl = cg::this_cluster();
     Team tm;
-    tm.rank = cl.block_rank();
-    tm.size = cl.num_blocks();
-    tm.tid = (int)tm.rank * blockDim.x + threadIdx.x;
-    tm.nthr = (int)tm.size * blockDim.x;
-    tm.wid = tm.tid >> 5;
-    tm.nwarps = tm.nthr >> 5;
+    tm.crank = cl.block_rank();
+    tm.csize = cl.num_blocks();
     tm.lane = threadIdx.x & 31;
+    tm.abort = abort;
+    const int cid = (int)(blockIdx.x / tm.csize);
+    auto form = [&](int k, int kidx) {
+        tm.k = k;
+        tm.kidx = kidx;
+        tm.rank = (unsigned)kidx * tm.csize + tm.crank;
+        tm.size = (unsigned)k * tm.csize;
+        tm.tid = (int)tm.rank * blockDim.x + threadIdx.x;
+        tm.nthr = (int)tm.size * blockDim.x;
+        tm.wid = tm.tid >> 5;
+        tm.nwarps = tm.nthr >> 5;
+    };
     if (threadIdx.x == 0) sh.red_buf = 0;  // every block of the team toggles it in step
     __syncthreads();
+    if (cid < nteams * kw && nwide > 0) {
+        const int t = cid / kw;
+        form(kw, cid % kw);
+        tm.bar = wbar + 2 * t;
+        tm.part = wpart + (size_t)t * 2 * kw * kRedMax;
+        tm.dec = wdec + (size_t)t * 16;
+        for (;;) {
+            if (tm.rank == 0 && threadIdx.x == 0) tm.dec[8] = (double)atomicAdd(queue + 1, 1);
+            team_sync(tm);
+            const int q = (int)__ldcg(tm.dec + 8);
+            team_sync(tm);
+            if (q >= nwide) break;
+            const int k = worder[q];
+            const Inst I = inst[k];
+            const Sys S = sys[I.sys];
+            Out o;
+            solve_instance(tm, sh, S, I, P, o);
+            if (*(volatile int *)abort) o.status = F3R_ERR_TIMEOUT;
+            if (tm.rank == 0 && threadIdx.x == 0) outs[k] = o;
+            team_sync(tm);
+        }
+    }
+    form(1, 0);
+    tm.bar = nullptr;
+    tm.part = nullptr;
+    tm.dec = nullptr;
     for (;;) {
         if (tm.rank == 0 && threadIdx.x == 0) sh.inst = atomicAdd(queue, 1);
-        team_sync();
+        team_sync(tm);
         const int q = cl.map_shared_rank(&sh, 0)->inst;
-        team_sync();
+        team_sync(tm);
         if (q >= ninst) break;
         const int k = order[q];
         const Inst I = inst[k];
@@ -721,7 +852,7 @@ __global__ void __launch_bounds__(kBT) k_batch(const Sys *sys, const Inst *inst,
         Out o;
         solve_instance(tm, sh, S, I, P, o);
         if (tm.rank == 0 && threadIdx.x == 0) outs[k] = o;
-        team_sync();
+        team_sync(tm);
     }
 }
 
@@ -733,14 +864,19 @@ using namespace f3r;
 struct f3r_batch {
     std::vector<Ctx *> sys;   // matrix of each system (set-up arrays only; none for a large system)
     std::vector<f3r_ctx *> full;  // large systems: a single-system context, else null
-    std::vector<int> small;   // instances of the persistent launch, largest first
+    std::vector<int> small;   // instances of the persistent launch on one cluster each, largest first
+    std::vector<int> wide;    // instances of the large systems taken by wide teams, largest first
     std::vector<int> nrhs;
     std::vector<int> inst_sys, inst_rhs;
     bt::BP P{};
     f3r_params prm{};
     bt::Sys *d_sys = nullptr;
     bt::Inst *d_inst = nullptr;
-    int *d_order = nullptr, *d_queue = nullptr;
+    int *d_order = nullptr, *d_queue = nullptr, *d_worder = nullptr, *d_abort = nullptr;
+    unsigned *d_wbar = nullptr;   // [team][2] barrier words of the wide teams
+    double *d_wpart = nullptr;    // [team][2][kw][kRedMax] cluster sums
+    double *d_wdec = nullptr;     // [team][16] broadcast slots
+    int kw = 0, nteams = 0;       // clusters per wide team, wide teams (of the last launch)
     bt::Out *d_out = nullptr;
     std::vector<bt::Inst> h_inst;
     std::vector<void *> allocs;
@@ -754,6 +890,7 @@ struct f3r_batch {
     bt::Out *pin_out = nullptr;
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int> graph_grid;  // blocks of each graph's launch
+    std::map<int, std::pair<int, int>> graph_wide;  // clusters per wide team, wide teams of each graph
     long long graph_launches = 0;
 };
 
@@ -806,6 +943,9 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
     // would run on one cluster and keep the launch waiting on them
     const long long split = prm.batch_split > 0 ? (long long)prm.batch_split
                                                 : (prm.batch_split < 0 ? (1LL << 40) : 2048LL * nsm);
+    // batch_wide < 0: the large systems on the single-system path; else in
+    // the persistent launch, each instance on a wide team of clusters
+    const bool single_path = prm.batch_wide < 0;
     b->full.assign(nsys, nullptr);
     std::vector<bt::Sys> hs(nsys);
     for (int k = 0; k < nsys; ++k) {
@@ -821,7 +961,7 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
         c->n = d.n;
         c->nnz = d.nnz;
         c->ld = (int)(((long long)d.n + kTileRows - 1) / kTileRows * kTileRows);  // whole tiles
-        if (d.n >= split) {
+        if (d.n >= split && single_path) {
             const f3r_status st = f3r_setup(&b->full[k], d.n, d.nnz, d.rowptr, d.colidx, d.val, &prm, (void *)s);
             if (st != F3R_OK) return fail(st);
             hs[k] = bt::Sys{};
@@ -907,14 +1047,31 @@ f3r_status f3r_setup_batched(f3r_batch **out, int nsys, const f3r_system_desc *d
     }
     std::memset(b->pin_out, 0, sizeof(bt::Out) * ninst);
     cudaMemcpyAsync(b->d_sys, hs.data(), sizeof(bt::Sys) * nsys, cudaMemcpyHostToDevice, s);
-    // the persistent launch's instances, largest first
-    for (int q = 0; q < ninst; ++q)
-        if (!b->full[b->inst_sys[q]]) b->small.push_back(q);
-    std::stable_sort(b->small.begin(), b->small.end(), [&](int a, int c) {
-        return b->sys[b->inst_sys[a]]->nnz > b->sys[b->inst_sys[c]]->nnz;
-    });
+    // the persistent launch's instances, largest first: the large systems'
+    // for the wide teams, the others for single clusters
+    for (int q = 0; q < ninst; ++q) {
+        if (b->full[b->inst_sys[q]]) continue;
+        if (b->sys[b->inst_sys[q]]->n >= split) b->wide.push_back(q);
+        else b->small.push_back(q);
+    }
+    auto larger = [&](int a, int c) { return b->sys[b->inst_sys[a]]->nnz > b->sys[b->inst_sys[c]]->nnz; };
+    std::stable_sort(b->small.begin(), b->small.end(), larger);
+    std::stable_sort(b->wide.begin(), b->wide.end(), larger);
     if (!b->small.empty())
         cudaMemcpyAsync(b->d_order, b->small.data(), sizeof(int) * b->small.size(), cudaMemcpyHostToDevice, s);
+    if (!b->wide.empty()) {
+        // barrier words, cluster sums and broadcast slots: a launch holds at
+        // most kMaxClustersPerSM clusters per SM, each in at most one team
+        const size_t maxc = (size_t)bt::kMaxClustersPerSM * nsm;
+        b->d_worder = (int *)balloc(b, sizeof(int) * b->wide.size());
+        b->d_wbar = (unsigned *)balloc(b, sizeof(unsigned) * 2 * maxc);
+        b->d_wpart = (double *)balloc(b, sizeof(double) * 2 * maxc * bt::kRedMax);
+        b->d_wdec = (double *)balloc(b, sizeof(double) * 16 * maxc);
+        if (!b->d_worder || !b->d_wbar || !b->d_wpart || !b->d_wdec) return fail(F3R_ERR_NOMEM);
+        cudaMemcpyAsync(b->d_worder, b->wide.data(), sizeof(int) * b->wide.size(), cudaMemcpyHostToDevice, s);
+    }
+    b->d_abort = (int *)balloc(b, sizeof(int) * 4);
+    if (!b->d_abort) return fail(F3R_ERR_NOMEM);
     b->P = bt::BP{m1, m2, m3, prm.c, prm.max_outer, prm.cgs_passes, prm.scale_cast, prm.tol, (float)prm.omega_fixed};
     b->cluster = 8;
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(F3R_ERR_CUDA);
@@ -945,8 +1102,8 @@ namespace {
 // through a pinned host table that the graph copies to the device.
 f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, f3r_batch_result *res,
                         std::vector<int> &st, void *stream) {
-    const int nsmall = (int)b->small.size();
-    if (nsmall == 0) return F3R_OK;
+    const int nsmall = (int)b->small.size(), nwide = (int)b->wide.size();
+    if (nsmall + nwide == 0) return F3R_OK;
     cudaStream_t s = b->cs;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -964,6 +1121,9 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
     const int key = cl * 1024 + nt;
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
+        int dev = 0, nsm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -981,7 +1141,14 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
             cudaGetLastError();
             ncl = 1;
         }
-        ncl = std::min(ncl, nsmall);
+        // every cluster resident at once (the wide teams' barriers need it)
+        ncl = std::min(ncl, bt::kMaxClustersPerSM * nsm);
+        if (nwide == 0) ncl = std::min(ncl, nsmall);
+        // wide teams: batch_wide clusters each (0: an eighth of the clusters, at least 2)
+        int kw = b->prm.batch_wide > 0 ? b->prm.batch_wide : std::max(2, ncl / 8);
+        kw = std::max(1, std::min(kw, ncl));
+        const int nteams = nwide > 0 ? std::max(1, std::min(nwide, ncl / kw)) : 0;
+        b->graph_wide[key] = std::make_pair(nwide > 0 ? kw : 0, nteams);
         cfg.gridDim = dim3(ncl * cl, 1, 1);
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
@@ -989,8 +1156,11 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
         if (e == cudaSuccess) {
             cudaMemcpyAsync(b->d_inst, b->pin_inst, sizeof(bt::Inst) * ninst, cudaMemcpyHostToDevice, s);
             cudaMemsetAsync(b->d_queue, 0, sizeof(int) * 4, s);
+            cudaMemsetAsync(b->d_abort, 0, sizeof(int) * 4, s);
+            if (nteams > 0) cudaMemsetAsync(b->d_wbar, 0, sizeof(unsigned) * 2 * nteams, s);
             cudaLaunchKernelEx(&cfg, bt::k_batch, (const bt::Sys *)b->d_sys, (const bt::Inst *)b->d_inst,
-                               (const int *)b->d_order, nsmall, b->P, b->d_queue, b->d_out);
+                               (const int *)b->d_order, nsmall, (const int *)b->d_worder, nwide, kw, nteams, b->P,
+                               b->d_queue, b->d_wbar, b->d_wpart, b->d_wdec, b->d_abort, b->d_out);
             cudaMemcpyAsync(b->pin_out, b->d_out, sizeof(bt::Out) * ninst, cudaMemcpyDeviceToHost, s);
             e = cudaStreamEndCapture(s, &g);
         }
@@ -1006,6 +1176,8 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
         b->graph_grid[key] = ncl * cl;
     }
     b->grid = b->graph_grid[key];
+    b->kw = b->graph_wide[key].first;
+    b->nteams = b->graph_wide[key].second;
     cudaEventRecord(e0, s);
     cudaError_t e = cudaGraphLaunch(it->second, s);
     b->graph_launches++;
@@ -1019,7 +1191,11 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
     const bt::Out *ho = b->pin_out;
-    for (int q : b->small) {
+    std::vector<int> all(b->small);
+    all.insert(all.end(), b->wide.begin(), b->wide.end());
+    std::vector<char> iswide(ninst, 0);
+    for (int q : b->wide) iswide[q] = 1;
+    for (int q : all) {
         st[q] = ho[q].status;
         if (res) {
             res[q].status = ho[q].status;
@@ -1031,7 +1207,7 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
             res[q].t_solve_ms = ms;
             res[q].system = b->inst_sys[q];
             res[q].rhs = b->inst_rhs[q];
-            res[q].path = 0;
+            res[q].path = iswide[q] ? 2 : 0;
         }
     }
     cudaEventRecord(e1, s);
@@ -1119,6 +1295,7 @@ f3r_status f3r_batched_autotune(f3r_batch *b, const double *const *B, double *co
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     b->graphs.clear();
     b->graph_grid.clear();
+    b->graph_wide.clear();
     for (int q = 0; q < ninst; ++q) cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
     cudaStreamSynchronize(b->cs);
     cudaEventDestroy(e0);
@@ -1143,12 +1320,23 @@ f3r_status f3r_batched_info(const f3r_batch *b, int64_t *out) {
     }
     out[0] = b->cluster;
     out[1] = b->threads;
-    out[2] = (int64_t)b->small.size();
+    out[2] = (int64_t)(b->small.size() + b->wide.size());
     out[3] = n_full;
     out[4] = rows_small;
     out[5] = rows_full;
     out[6] = b->grid;
     out[7] = b->graph_launches;
+    return F3R_OK;
+}
+
+f3r_status f3r_batched_wide_info(const f3r_batch *b, int64_t *out) {
+    if (!b || !out) return F3R_ERR_ARG;
+    long long rows = 0;
+    for (int q : b->wide) rows += b->sys[b->inst_sys[q]]->n;
+    out[0] = b->kw;
+    out[1] = b->nteams;
+    out[2] = (int64_t)b->wide.size();
+    out[3] = rows;
     return F3R_OK;
 }
 

@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("row_scale", C.c_int), ("scale_cast", C.c_int), ("cgs_passes", C.c_int), ("tol", C.c_double),
         ("max_outer", C.c_int), ("use_graphs", C.c_int), ("keep_omega", C.c_int), ("fuse_cgs", C.c_int),
         ("inner_rtol", C.c_float), ("ainv_alpha", C.c_float),
-        ("fuse_step", C.c_int), ("batch_split", C.c_int), ("reserved", C.c_int * 2),
+        ("fuse_step", C.c_int), ("batch_split", C.c_int), ("batch_wide", C.c_int), ("reserved", C.c_int),
     ]
 
 
@@ -110,6 +110,7 @@ def lib():
         L.f3r_batched_instances.restype = C.c_int
         L.f3r_batched_set_shape.argtypes = [vp, C.c_int, C.c_int]
         L.f3r_batched_info.argtypes = [vp, C.POINTER(C.c_int64)]
+        L.f3r_batched_wide_info.argtypes = [vp, C.POINTER(C.c_int64)]
         L.f3r_batched_device_bytes.argtypes = [vp]
         L.f3r_batched_device_bytes.restype = C.c_int64
         L.f3r_destroy_batched.argtypes = [vp]
@@ -405,9 +406,10 @@ class Solver:
 
 class BatchedSolver:
     """Many systems (each with nrhs right-hand sides): f3r_setup_batched /
-    f3r_solve_batched.  Instances of systems below params.batch_split rows are
-    solved in one persistent launch (one thread-block cluster each), larger
-    systems one after another by the single-system path."""
+    f3r_solve_batched.  Every instance is solved in one persistent launch:
+    systems below params.batch_split rows on one thread-block cluster each,
+    larger systems on wide teams of params.batch_wide clusters (or, with
+    batch_wide < 0, one after another by the single-system path)."""
 
     def __init__(self, systems, params: Params = None, stream=None):
         """systems: list of (rowptr, colidx, val, nrhs) with host (numpy) or
@@ -438,6 +440,12 @@ class BatchedSolver:
         keys = ("cluster", "threads", "instances_launch", "instances_single", "rows_launch", "rows_single",
                 "grid", "graph_launches")
         return {k: int(v) for k, v in zip(keys, out)}
+
+    def wide_info(self) -> dict:
+        """The wide teams of the last launch (f3r_batched_wide_info)."""
+        out = (C.c_int64 * 4)()
+        _check(lib().f3r_batched_wide_info(self.h, out), "f3r_batched_wide_info")
+        return {k: int(v) for k, v in zip(("clusters_per_team", "teams", "instances", "rows"), out)}
 
     def autotune(self, B, X, stream=None) -> int:
         """Pick the team shape (cluster size, threads per block) by timing one

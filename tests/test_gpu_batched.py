@@ -66,13 +66,14 @@ def test_batched_instance_matches_oracle(batch):
 
 
 def test_batched_split_large_systems_to_single_path(batch):
-    """Systems of at least batch_split rows are solved one after another by the
-    single-system path: their results are bit for bit those of a separate
-    f3r_solve; the rest still go through the persistent launch and converge."""
+    """With batch_wide < 0, systems of at least batch_split rows are solved one
+    after another by the single-system path: their results are bit for bit
+    those of a separate f3r_solve; the rest still go through the persistent
+    launch and converge."""
     split = 5000
     assert any(p.n >= split for p, _ in batch) and any(p.n < split for p, _ in batch)
     systems = [(dev(p.rowptr), dev(p.colidx), dev(p.val), B.shape[0]) for p, B in batch]
-    bs = f3r.BatchedSolver(systems, f3r.default_params(batch_split=split))
+    bs = f3r.BatchedSolver(systems, f3r.default_params(batch_split=split, batch_wide=-1))
     Bs, Xs, meta = [], [], []
     for k, (p, B) in enumerate(batch):
         for r in range(B.shape[0]):
@@ -152,13 +153,13 @@ def test_batched_autotune_picks_a_shape(batch):
 
 
 def test_batched_large_systems_next_to_the_launch(batch):
-    """With batch_split below some systems' size, those instances run on the
-    single-system path while the persistent launch runs beside them: every
-    instance is still solved, each path reports itself."""
+    """With batch_split below some systems' size and batch_wide < 0, those
+    instances run on the single-system path beside the persistent launch:
+    every instance is still solved, each path reports itself."""
     systems = [(dev(p.rowptr), dev(p.colidx), dev(p.val), B.shape[0]) for p, B in batch]
     ns = sorted(p.n for p, _ in batch)
     split = ns[len(ns) // 2]
-    bs = f3r.BatchedSolver(systems, f3r.default_params(batch_split=split))
+    bs = f3r.BatchedSolver(systems, f3r.default_params(batch_split=split, batch_wide=-1))
     Bs, Xs, meta = _instances(batch)
     code, res = bs.solve(Bs, Xs)
     torch.cuda.synchronize()
@@ -170,4 +171,43 @@ def test_batched_large_systems_next_to_the_launch(batch):
         rel = np.linalg.norm(B[r] - p.to_scipy() @ Xs[q].cpu().numpy()) / np.linalg.norm(B[r])
         assert res[q].status == f3r.OK and rel < 1e-9, (q, rel)
         assert res[q].path == (1 if p.n >= split else 0)
+    bs.close()
+
+
+@pytest.mark.parametrize("cluster,wide", [(1, 2), (2, 3), (1, 0)])
+def test_batched_wide_teams_all_in_one_launch(batch, cluster, wide):
+    """Every instance in the one persistent launch: the large systems' on wide
+    teams of several clusters (global-memory barriers, cluster sums added in
+    cluster order), the others on one cluster each.  Each instance converges
+    to 1e-9 within one outer iteration of its single-system solve, reports its
+    path, and a solve is one graph replay with no single-system work."""
+    systems = [(dev(p.rowptr), dev(p.colidx), dev(p.val), B.shape[0]) for p, B in batch]
+    ns = sorted(p.n for p, _ in batch)
+    split = ns[len(ns) // 2]
+    bs = f3r.BatchedSolver(systems, f3r.default_params(batch_split=split, batch_wide=wide))
+    bs.set_shape(cluster, 512)
+    Bs, Xs, meta = _instances(batch)
+    g0 = bs.info()["graph_launches"]
+    code, res = bs.solve(Bs, Xs)
+    torch.cuda.synchronize()
+    assert code == f3r.OK
+    info, wi = bs.info(), bs.wide_info()
+    assert info["instances_single"] == 0 and info["instances_launch"] == len(meta)
+    assert info["graph_launches"] == g0 + 1
+    assert wi["teams"] >= 1 and wi["instances"] == sum(B.shape[0] for p, B in batch if p.n >= split)
+    if wide > 0:
+        assert wi["clusters_per_team"] == wide
+    for q, (k, r) in enumerate(meta):
+        p, B = batch[k]
+        rel = np.linalg.norm(B[r] - p.to_scipy() @ Xs[q].cpu().numpy()) / np.linalg.norm(B[r])
+        assert res[q].status == f3r.OK and rel < 1e-9, (q, rel)
+        assert abs(rel - res[q].rel_res_true) <= 1e-12
+        assert res[q].path == (2 if p.n >= split else 0)
+        assert res[q].m_applies == 64 * res[q].outer_iters
+        if p.n >= split:
+            s = f3r.Solver(dev(p.rowptr), dev(p.colidx), dev(p.val), f3r.default_params())
+            xs = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+            rs = s.solve(dev(B[r]), xs)
+            assert abs(rs.outer_iters - res[q].outer_iters) <= 1
+            s.close()
     bs.close()
