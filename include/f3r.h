@@ -347,9 +347,10 @@ f3r_status f3r_batched_set_cluster(f3r_batch *batch, int cluster_size);
 f3r_status f3r_batched_set_shape(f3r_batch *batch, int cluster_size, int threads);
 /* Autotuner: times one outer iteration of the persistent launch's instances
  * (from x0 = 0) for every team shape (cluster sizes 1, 2, 4, 8 times 256 or
- * 512 threads per block) and keeps the fastest (its cluster size written to
- * *chosen if not NULL; f3r_batched_info gives both).  B and X as in
- * f3r_solve_batched; X is zero on return. */
+ * 512 threads per block; with large systems and batch_wide = 0 also 2, 4 or
+ * 8 clusters per wide team) and keeps the fastest (its cluster size written
+ * to *chosen if not NULL; f3r_batched_info and f3r_batched_wide_info give
+ * the rest).  B and X as in f3r_solve_batched; X is zero on return. */
 f3r_status f3r_batched_autotune(f3r_batch *batch, const double *const *B, double *const *X, int *chosen,
                                 void *stream);
 int f3r_batched_instances(const f3r_batch *batch);

@@ -877,6 +877,7 @@ struct f3r_batch {
     double *d_wpart = nullptr;    // [team][2][kw][kRedMax] cluster sums
     double *d_wdec = nullptr;     // [team][16] broadcast slots
     int kw = 0, nteams = 0;       // clusters per wide team, wide teams (of the last launch)
+    int kw_req = 0;               // clusters per wide team the autotuner chose (0: batch_wide's rule)
     bt::Out *d_out = nullptr;
     std::vector<bt::Inst> h_inst;
     std::vector<void *> allocs;
@@ -1118,7 +1119,8 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
     // the graph reads the table from pinned memory when it runs
     std::memcpy(b->pin_inst, b->h_inst.data(), sizeof(bt::Inst) * ninst);
     const int cl = b->cluster, nt = b->threads;
-    const int key = cl * 1024 + nt;
+    const int kw_code = b->kw_req > 0 ? b->kw_req : std::max(0, b->prm.batch_wide);  // 0: automatic
+    const int key = (kw_code * 16 + cl) * 1024 + nt;
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         int dev = 0, nsm = 1;
@@ -1145,7 +1147,7 @@ f3r_status launch_small(f3r_batch *b, const double *const *B, double *const *X, 
         ncl = std::min(ncl, bt::kMaxClustersPerSM * nsm);
         if (nwide == 0) ncl = std::min(ncl, nsmall);
         // wide teams: batch_wide clusters each (0: an eighth of the clusters, at least 2)
-        int kw = b->prm.batch_wide > 0 ? b->prm.batch_wide : std::max(2, ncl / 8);
+        int kw = kw_code > 0 ? kw_code : std::max(2, ncl / 8);
         kw = std::max(1, std::min(kw, ncl));
         const int nteams = nwide > 0 ? std::max(1, std::min(nwide, ncl / kw)) : 0;
         b->graph_wide[key] = std::make_pair(nwide > 0 ? kw : 0, nteams);
@@ -1256,41 +1258,53 @@ f3r_status f3r_solve_batched(f3r_batch *b, const double *const *B, double *const
 // Autotuner of the batched launch shape: time one outer iteration of the
 // persistent launch's instances (from x0 = 0) for every team shape -- blocks
 // per instance (the cluster size: 1, 2, 4, 8) times threads per block (256,
-// 512), i.e. the rows each thread of a team covers -- and keep the fastest.
-// X is zeroed again on return.  The graphs made while timing stay cached.
+// 512), i.e. the rows each thread of a team covers -- and, when the batch has
+// large systems and batch_wide is automatic, clusters per wide team (2, 4,
+// 8); keep the fastest.  X is zeroed again on return.
 f3r_status f3r_batched_autotune(f3r_batch *b, const double *const *B, double *const *X, int *chosen, void *stream) {
     if (!b || !B || !X) return F3R_ERR_ARG;
     const int saved_outer = b->P.max_outer;
     const int cand[8][2] = {{1, 256}, {1, 512}, {2, 256}, {2, 512}, {4, 256}, {4, 512}, {8, 256}, {8, 512}};
+    // clusters per wide team, when the batch has large systems and batch_wide is automatic
+    std::vector<int> kws{0};
+    if (!b->wide.empty() && b->prm.batch_wide == 0) kws = {2, 4, 8};
     float best = 3.0e38f;
-    int best_c = b->cluster, best_t = b->threads;
+    int best_c = b->cluster, best_t = b->threads, best_kw = b->kw_req;
     const int ninst = (int)b->h_inst.size();
+    std::vector<int> in_launch(b->small);
+    in_launch.insert(in_launch.end(), b->wide.begin(), b->wide.end());
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     for (int ci = 0; ci < 8; ++ci) {
-        b->cluster = cand[ci][0];
-        b->threads = cand[ci][1];
-        b->P.max_outer = 1;
-        for (int q : b->small) cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
-        cudaEventRecord(e0, b->cs);
-        std::vector<int> stv(ninst, F3R_OK);
-        f3r_status st = launch_small(b, B, X, nullptr, stv, stream);
-        for (int q : b->small)
-            if (st == F3R_OK && stv[q] != F3R_OK) st = (f3r_status)stv[q];
-        cudaEventRecord(e1, b->cs);
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if ((st == F3R_OK || st == F3R_NOT_CONVERGED) && ms < best) {
-            best = ms;
-            best_c = cand[ci][0];
-            best_t = cand[ci][1];
+        for (int kw : kws) {
+            b->cluster = cand[ci][0];
+            b->threads = cand[ci][1];
+            b->kw_req = kw;
+            b->P.max_outer = 1;
+            for (int q : in_launch)
+                cudaMemsetAsync(X[q], 0, sizeof(double) * (size_t)b->sys[b->inst_sys[q]]->n, b->cs);
+            cudaEventRecord(e0, b->cs);
+            std::vector<int> stv(ninst, F3R_OK);
+            f3r_status st = launch_small(b, B, X, nullptr, stv, stream);
+            for (int q : in_launch)
+                if (st == F3R_OK && stv[q] != F3R_OK) st = (f3r_status)stv[q];
+            cudaEventRecord(e1, b->cs);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if ((st == F3R_OK || st == F3R_NOT_CONVERGED) && ms < best) {
+                best = ms;
+                best_c = cand[ci][0];
+                best_t = cand[ci][1];
+                best_kw = kw;
+            }
         }
     }
     b->P.max_outer = saved_outer;
     b->cluster = best_c;
     b->threads = best_t;
+    b->kw_req = best_kw;
     // the graphs captured while tuning hold max_outer = 1: drop them
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     b->graphs.clear();

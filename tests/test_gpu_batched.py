@@ -187,6 +187,8 @@ def test_batched_wide_teams_all_in_one_launch(batch, cluster, wide):
     bs = f3r.BatchedSolver(systems, f3r.default_params(batch_split=split, batch_wide=wide))
     bs.set_shape(cluster, 512)
     Bs, Xs, meta = _instances(batch)
+    if wide == 0:  # automatic: the autotuner also picks the clusters per wide team
+        bs.autotune(Bs, Xs)
     g0 = bs.info()["graph_launches"]
     code, res = bs.solve(Bs, Xs)
     torch.cuda.synchronize()
@@ -197,6 +199,8 @@ def test_batched_wide_teams_all_in_one_launch(batch, cluster, wide):
     assert wi["teams"] >= 1 and wi["instances"] == sum(B.shape[0] for p, B in batch if p.n >= split)
     if wide > 0:
         assert wi["clusters_per_team"] == wide
+    else:
+        assert wi["clusters_per_team"] in (2, 4, 8)
     for q, (k, r) in enumerate(meta):
         p, B = batch[k]
         rel = np.linalg.norm(B[r] - p.to_scipy() @ Xs[q].cpu().numpy()) / np.linalg.norm(B[r])
