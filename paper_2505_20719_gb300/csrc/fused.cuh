@@ -374,6 +374,7 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedThreads <= 512 ? 2 : 1)
     double *ws = reinterpret_cast<double *>(fused_dsm);
     __shared__ double hs[kMaxOuterM + 1];
     __shared__ double tot[kOuterGroup + 1];
+    __shared__ double wsum[kOuterGroup][kFusedWarps];  // the warps' sums of up to kOuterGroup dot products
     const int j = *L.jptr;
     const int nv = j + 1;
     const int G = gridDim.x;
@@ -393,39 +394,45 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedThreads <= 512 ? 2 : 1)
     // The block's rows of each basis vector are streamed one vector at a time
     // (one contiguous run per block in flight, kOuterUnroll packs per thread),
     // with the same fma order per sum and per element as a row-major sweep.
-    // dots V[0..nv)^T ws into part[l * G + block]
+    // dots V[0..nv)^T ws into part[l * G + block]: a thread's sum over its
+    // packs, the warp's butterfly sum, the warps' sums in warp order (one
+    // vector loop, so that the sweep's code is not repeated per vector)
     auto dots = [&](double *part) {
-        for (int l0 = 0; l0 < nv; l0 += kOuterGroup) {
-            double acc[kOuterGroup];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+        for (int l = 0; l < nv; ++l) {
+            const double *__restrict__ Vl = V + (size_t)l * L.ld;
+            double a = 0.0;
+            for (int q0 = threadIdx.x; q0 < nq; q0 += blockDim.x * kOuterUnroll) {
+                Pack<double, N> v[kOuterUnroll];
 #pragma unroll
-            for (int k = 0; k < kOuterGroup; ++k) acc[k] = 0.0;
+                for (int u = 0; u < kOuterUnroll; ++u) {
+                    const int q = q0 + u * (int)blockDim.x;
+                    if (q < nq) v[u] = ldp<double, N>(Vl + (size_t)q * N);
+                }
 #pragma unroll
-            for (int k = 0; k < kOuterGroup; ++k) {
-                if (l0 + k < nv) {
-                    const double *__restrict__ Vl = V + (size_t)(l0 + k) * L.ld;
-                    for (int q0 = threadIdx.x; q0 < nq; q0 += blockDim.x * kOuterUnroll) {
-                        Pack<double, N> v[kOuterUnroll];
+                for (int u = 0; u < kOuterUnroll; ++u) {
+                    const int q = q0 + u * (int)blockDim.x;
+                    if (q < nq) {
+                        const Pack<double, N> wv = ldp<double, N>(ws + (size_t)q * N);
 #pragma unroll
-                        for (int u = 0; u < kOuterUnroll; ++u) {
-                            const int q = q0 + u * (int)blockDim.x;
-                            if (q < nq) v[u] = ldp<double, N>(Vl + (size_t)q * N);
-                        }
-#pragma unroll
-                        for (int u = 0; u < kOuterUnroll; ++u) {
-                            const int q = q0 + u * (int)blockDim.x;
-                            if (q < nq) {
-                                const Pack<double, N> wv = ldp<double, N>(ws + (size_t)q * N);
-#pragma unroll
-                                for (int e = 0; e < N; ++e) acc[k] = fma_rn(v[u].v[e], wv.v[e], acc[k]);
-                            }
-                        }
+                        for (int e = 0; e < N; ++e) a = fma_rn(v[u].v[e], wv.v[e], a);
                     }
-                    for (int i = nq * N + threadIdx.x; i < cnt; i += blockDim.x) acc[k] = fma_rn(Vl[i], ws[i], acc[k]);
                 }
             }
-            block_reduce<double, kOuterGroup>(acc, min(kOuterGroup, nv - l0), false, tot);
-            if (threadIdx.x < kOuterGroup && l0 + (int)threadIdx.x < nv)
-                part[(size_t)(l0 + threadIdx.x) * G + blockIdx.x] = tot[threadIdx.x];
+            for (int i = nq * N + threadIdx.x; i < cnt; i += blockDim.x) a = fma_rn(Vl[i], ws[i], a);
+            a = warp_sum(a);
+            const int k = l % kOuterGroup;
+            if (lane == 0) wsum[k][warp] = a;
+            if (k == kOuterGroup - 1 || l == nv - 1) {
+                __syncthreads();
+                if ((int)threadIdx.x <= k) {
+                    double sm = wsum[threadIdx.x][0];
+                    for (int w = 1; w < kFusedWarps; ++w) sm = add_rn(sm, wsum[threadIdx.x][w]);
+                    part[(size_t)(l - k + threadIdx.x) * G + blockIdx.x] = sm;
+                }
+                __syncthreads();
+            }
         }
     };
     // hs[l] = sum over blocks of part[l * G + b] (fixed order, every block alike)
@@ -512,9 +519,13 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedThreads <= 512 ? 2 : 1)
         }
         const double inv = (hn > 0.0 && isfinite(hn)) ? div_rn(1.0, hn) : inv_prev;
         double *out = L.V + (size_t)(j + 1) * L.ld + r0;
+        // block 0's thread 0 runs the Givens step (a serial chain of fp64
+        // operations) above while its other warps take the block's rows
+        const int r_first = (blockIdx.x == 0) ? (int)threadIdx.x - 32 : (int)threadIdx.x;
+        const int r_step = (blockIdx.x == 0) ? (int)blockDim.x - 32 : (int)blockDim.x;
         if constexpr (CHILD == CHILD_F) {
             TC cacc[2] = {(TC)0, (TC)0};
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            for (int i = r_first; i >= 0 && i < cnt; i += r_step) {
                 const double v = mul_rn(ws[i], inv);
                 const TC c = co.dsc ? Store<TC>::from(mul_rn(co.dsc[r0 + i], v)) : Store<TC>::from(v);
                 out[i] = v;
@@ -545,7 +556,7 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedThreads <= 512 ? 2 : 1)
                 }
             });
         } else {
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = mul_rn(ws[i], inv);
+            for (int i = r_first; i >= 0 && i < cnt; i += r_step) out[i] = mul_rn(ws[i], inv);
         }
         // every block read j at its start: close outer iteration j
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(const_cast<int *>(L.jptr), 1);
