@@ -1,17 +1,20 @@
 // Batched F3R: many systems and right-hand sides in one persistent launch.
 //
 // Every (system, right-hand side) instance is solved entirely on the device
-// by one thread-block cluster ("team"): the outer fp64 FGMRES(m1) with its
+// by a team: one thread-block cluster, or for the large systems a wide team
+// of several clusters.  A team runs the outer fp64 FGMRES(m1) with its
 // convergence test and restarts, the fp32 FGMRES(m2), the FGMRES(m3) with
 // fp16 A and the fp16 Richardson R_2 with adaptive weights (Sec. 4.2,
 // Table 1, Algorithm 1) -- the same arithmetic as the single-system path.
-// Kernel boundaries become cluster barriers (barrier.cluster), reductions sum
-// per-block partials in distributed shared memory in a fixed rank order, and
-// the small Givens / least-squares state of the inner levels is kept, and
-// updated identically, in every block of the team.  Clusters take instances
-// from an atomic work queue ordered by size (largest first).  All control
-// decisions derive from values every block of a team holds identically, so
-// every block reaches every cluster barrier.
+// Kernel boundaries become cluster barriers (barrier.cluster), plus, in a
+// wide team, a bounded barrier of the clusters in global memory; reductions
+// sum per-block partials in distributed shared memory in a fixed rank order
+// (and a wide team's cluster sums in cluster order); the small Givens /
+// least-squares state of the inner levels is kept, and updated identically,
+// in every block of the team.  Teams take instances from atomic work queues
+// ordered by size (largest first).  All control decisions derive from values
+// every block of a team holds identically, so every block reaches every
+// barrier.
 //
 // Data written inside the launch is read with ld.global.cg (L2), never through
 // the non-coherent read-only path.
