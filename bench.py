@@ -635,7 +635,25 @@ def main():
         "f3_step_L2": 2 * (ib + asz) * ns + 2 * rsb + vsz * n + msz * n + 4 * n + 4 * n + 4 * n * 2.5 + 4 * n + vsz * n,
     }
     ranked = sorted(prof, key=lambda k: -prof[k]["ms"])
+    # the roofline object covers the kernel the metric names -- the fp16 SpMV
+    # and the fused Richardson call -- that takes the largest share; the top
+    # three kernels of any kind follow in `rooflines`, the fp32 CGS2 passes
+    # with the per-step bytes 4n(3j + 4) of the byte model (j averaged over
+    # the level's iterations)
     dk = next((k for k in ranked if k in algo), None)
+    cgs_bytes = {"cgs_fused_L2": 4 * n * (3 * 1.5 + 4), "cgs_fused_L1": 4 * n * (3 * 3.5 + 4)}
+    rooflines = []
+    for k in ranked[:3]:
+        b_k = algo.get(k, cgs_bytes.get(k))
+        if b_k is None:
+            rooflines.append({"kernel": k, "share": prof[k]["share"], "avg_launch_us": prof[k]["avg_us"],
+                              "bytes_per_launch": None})
+            continue
+        ach = b_k / (prof[k]["avg_us"] * 1e-6) / 1e9
+        rooflines.append({"kernel": k, "share": prof[k]["share"], "avg_launch_us": prof[k]["avg_us"],
+                          "bytes_per_launch": b_k, "achieved_gbs": ach, "frac": ach / hbm,
+                          "bound": ("grid barriers and L2 latency (cooperative launch, two grid barriers)"
+                                    if k.startswith("cgs_fused") else "hbm / tile pipeline")})
     avg_s = prof[dk]["avg_us"] * 1e-6
     achieved = algo[dk] / avg_s / 1e9
     roofline = {"bound": "hbm", "kernel": dk, "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -648,7 +666,9 @@ def main():
                 "stored_format": ("windowed SELL-32, 2-byte window indices, 512-row tiles" if info["windowed"]
                                   else "SELL-32, int32 columns"),
                 "time_source": "CUDA events around each launch of one profiled solve (launches not "
-                               "overlapped, so each time includes its launch gap)"}
+                               "overlapped, so each time includes its launch gap)",
+                "selection": "the largest-share kernel among the fp16 SpMV and Richardson kernels the "
+                             "metric names; `rooflines` lists the top three kernels of the solve"}
 
     # ---- stand-alone 16-bit SpMV (f3r_spmv), the metric's second half
     sp_prec = {"fp16-F3R": f3r.F16, "bf16-F3R": f3r.BF16, "fp32-F3R": f3r.F32}.get(args.kind, f3r.F64)
@@ -782,7 +802,7 @@ def main():
         "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
         "config": _config(args, prob, ws),
         "outer_iters": last.outer_iters, "rel_res_true": true_rel, "status": f3r.STATUS.get(last.status),
-        "roofline": roofline, "spmv_fp16": spmv, "kernels": prof, "comparators": comparators,
+        "roofline": roofline, "rooflines": rooflines, "spmv_fp16": spmv, "kernels": prof, "comparators": comparators,
         "level_errors": level_errors, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         "device_bytes": s.device_bytes,
     }
