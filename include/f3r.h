@@ -195,6 +195,16 @@ f3r_status f3r_set_rich_state(f3r_ctx *ctx, const double *omega8, int64_t c_ntr)
  * Returns F3R_ERR_ARG if the array does not exist. */
 f3r_status f3r_export(f3r_ctx *ctx, int which, void *out);
 
+/* Round n fp32 values x to prec (F3R_F16 or F3R_BF16) with the conversion
+ * every kernel of this library applies when it stores a 16-bit value (round
+ * to nearest, ties to even, subnormals kept, overflow to infinity; Table 1's
+ * fp16 storage, and bf16 in its place), writing the 16-bit patterns to out
+ * (test entry: it lets a test compare the device conversion with an
+ * independent definition over every fp32 bit pattern).  x and out are device
+ * pointers, asynchronous on stream.  Errors: F3R_ERR_ARG (prec, n < 0, null
+ * pointers), F3R_ERR_CUDA. */
+f3r_status f3r_round16(int prec, const float *x, uint16_t *out, int64_t n, void *stream);
+
 /* Storage of the set-up matrix (instrumentation), out[8]:
  *   [0] 1 if the matrix is windowed (below), [1] largest window of a tile
  *   (entries), [2] stored SELL entries (padding included), [3] widest slice,

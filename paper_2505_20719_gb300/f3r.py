@@ -125,6 +125,8 @@ def lib():
         for name in ("f3r_learned_load", "f3r_learned_get", "f3r_learned_apply", "f3r_learned_loss_grad",
                      "f3r_learned_train", "f3r_learned_set_loss"):
             getattr(L, name).restype = C.c_int
+        L.f3r_round16.argtypes = [C.c_int, vp, vp, C.c_int64, vp]
+        L.f3r_round16.restype = C.c_int
         L.f3r_residual_noalloc.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.f3r_residual_noalloc.restype = C.c_int
         for name in ("f3r_default_params", "f3r_setup", "f3r_solve", "f3r_spmv", "f3r_apply",
@@ -402,6 +404,13 @@ class Solver:
         _check(lib().f3r_matrix_info(self.h, out), "f3r_matrix_info")
         keys = ("windowed", "win_max", "nsell", "wmax", "nslices", "index_bytes", "win_chunk", "m_unit")
         return {k: int(v) for k, v in zip(keys, out)}
+
+
+def round16(prec: int, x, out, stream=None):
+    """f3r_round16: the library's fp32 -> 16-bit store conversion of device
+    array x (float32) into out (16-bit patterns, int16 or uint16 storage)."""
+    _check(lib().f3r_round16(prec, _ptr(x), _ptr(out), int(x.numel()), _stream(stream)), "f3r_round16")
+    return out
 
 
 class BatchedSolver:
