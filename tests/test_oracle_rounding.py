@@ -4,7 +4,8 @@ The oracle rounds from the IEEE 754 definition (spacing of the binade,
 nearbyint, gradual underflow, overflow to infinity).  It is checked against
 independent sources: numpy's float16 conversion, torch's bfloat16 conversion,
 the classic bit-level round-to-nearest-even formula for bfloat16, and
-hand-worked values.
+hand-worked values; fp32 -> fp16 / bf16 on every one of the 2^32 fp32 bit
+patterns.
 """
 import numpy as np
 import pytest
@@ -125,3 +126,37 @@ def test_every_float32_binade_and_sign_at_stride_256(orc):
     assert np.all(same) and np.array_equal(np.signbit(got16), np.signbit(want16))
     gotbf = O.round_to(O.BF16, x64)
     assert np.array_equal(gotbf, _bf16_bits_rne(x32))
+
+
+def _all_patterns_piece(start, count):
+    """mismatches of the oracle's fp16 and bf16 rounding against numpy's fp16
+    cast and the bit-level bf16 formula on fp32 patterns start .. start + count - 1"""
+    u = (np.arange(start, start + count, dtype=np.uint64) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    x32 = u.view(np.float32)
+    fin = np.isfinite(x32)
+    x64 = x32.astype(np.float64)
+    got16 = O.round_to(O.F16, x64)
+    with np.errstate(over="ignore", invalid="ignore"):
+        want16 = x32.astype(np.float16).astype(np.float64)
+    bad = int(np.count_nonzero((got16 != want16) & fin))
+    bad += int(np.count_nonzero(np.signbit(got16[fin]) != np.signbit(want16[fin])))
+    gotbf = O.round_to(O.BF16, x64)
+    bf = ((u + np.uint32(0x7FFF) + ((u >> np.uint32(16)) & np.uint32(1))) >> np.uint32(16)) << np.uint32(16)
+    wantbf = bf.view(np.float32).astype(np.float64)
+    bad += int(np.count_nonzero((gotbf != wantbf) & fin))
+    # inf and nan in, the same out
+    bad += int(np.count_nonzero(np.isnan(x64) != np.isnan(got16)) + np.count_nonzero(np.isnan(x64) != np.isnan(gotbf)))
+    return bad
+
+
+def test_every_float32_pattern(orc):
+    """The oracle's fp32 -> fp16 and fp32 -> bf16 rounding against numpy's
+    float16 cast and the bit-level round-to-nearest-even bfloat16 formula on
+    all 2^32 fp32 bit patterns (NaN in, NaN out), in pieces across threads
+    (the oracle's C loop and numpy release the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    piece = 1 << 24
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        bad = sum(ex.map(lambda s: _all_patterns_piece(s, piece), range(0, 1 << 32, piece)))
+    assert bad == 0, bad
